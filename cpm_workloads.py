@@ -1,0 +1,310 @@
+"""Seeded synthetic workloads for the cellular Potts model (CPM) sweep.
+
+This module only produces inputs: an initial int32 cell-id lattice, the
+per-cell type table and the integer-scaled model parameters.  It holds no
+part of the CPM's arithmetic (no energies, no acceptance, no tallies), so the
+CPU oracle and the CUDA path can both consume it without sharing any of the
+method's code.
+
+Conventions shared by every consumer (they are data conventions, not code):
+
+* lattice layout: x fastest, then y, then z (``idx = x + nx*(y + ny*z)``);
+  2D lattices have ``nz == 1``;
+* cell id 0 is the medium (type 0); ids 1..n_cells are cells; a negative id
+  (-1) is a frozen obstacle ("fibre") site whose type is ``obstacle_type``;
+* energies are integers: every J and lambda of the paper's model (Methods,
+  Eq. 1 and the perimeter term) is multiplied by an integer scale ``S`` so
+  that all of them become integers, and the temperature T is multiplied by
+  the same S;
+* checkerboard parameters: ``a`` is the edge of one schedule area, ``c`` the
+  number of checkerboard divisions per axis (so ``c**dim`` colours and active
+  blocks of edge ``s = a // c``), ``P`` the number of colour cycles per MCS.
+
+The paper's own tissues come from segmented microscopy, which is not
+available; the generators below stand in for them with seeded shapes of the
+same kind (point or cube cells at blue-noise centres; a Voronoi-edge fibre
+network for the stromal obstacle).
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Optional
+
+import numpy as np
+
+MAX_TYPES = 8
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    dim: int
+    nx: int
+    ny: int
+    nz: int
+    J: np.ndarray            # int32 [MAX_TYPES, MAX_TYPES], symmetric, scaled
+    lambda_v: np.ndarray     # int32 [MAX_TYPES], scaled
+    v_target: np.ndarray     # int32 [MAX_TYPES]
+    lambda_p: np.ndarray     # int32 [MAX_TYPES], scaled
+    a_target: np.ndarray     # int32 [MAX_TYPES]
+    lambda_act: np.ndarray   # int32 [MAX_TYPES], scaled
+    max_act: np.ndarray      # int32 [MAX_TYPES]
+    T: float                 # temperature, scaled by the same S
+    scale: int               # the integer energy scale S
+    a: int
+    c: int
+    P: int
+    seed: int
+    obstacle_type: int
+    lattice: np.ndarray      # int32 [nz, ny, nx] (x fastest)
+    cell_type: np.ndarray    # uint8 [n_cells + 1]; entry 0 is the medium
+    act: Optional[np.ndarray] = None  # uint8 [nz, ny, nx] initial Act values
+    n_mcs: int = 1
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.cell_type.shape[0] - 1)
+
+    @property
+    def n_sites(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def act_on(self) -> bool:
+        return bool(np.any(self.lambda_act != 0))
+
+    def replace(self, **kw) -> "Workload":
+        return dataclasses.replace(self, **kw)
+
+
+def _params(n_types: int = 3):
+    z = lambda: np.zeros(MAX_TYPES, dtype=np.int32)  # noqa: E731
+    return (np.zeros((MAX_TYPES, MAX_TYPES), dtype=np.int32), z(), z(), z(), z(), z(), z())
+
+
+def _sym(J, a, b, v):
+    J[a, b] = v
+    J[b, a] = v
+
+
+# --------------------------------------------------------------------------
+# seeding helpers
+# --------------------------------------------------------------------------
+
+def jittered_centres(shape, spacing: float, jitter: float, rng) -> np.ndarray:
+    """Blue-noise centres: one point per cell of a regular grid of the given
+    spacing, displaced uniformly by at most ``jitter`` per axis.  Any two
+    centres are at least ``spacing - 2*jitter`` apart along some axis."""
+    axes = []
+    for n in shape:
+        m = max(1, int(round(n / spacing)))
+        axes.append((np.arange(m) + 0.5) * (n / m))
+    grid = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1).reshape(-1, len(shape))
+    grid = grid + rng.uniform(-jitter, jitter, size=grid.shape)
+    pts = np.floor(grid).astype(np.int64)
+    for d, n in enumerate(shape):
+        pts[:, d] %= n
+    return pts
+
+
+def place_cubes(lattice: np.ndarray, centres: np.ndarray, edge: int) -> int:
+    """Write cubes (squares in 2D) of the given edge, periodic, with ids
+    1..len(centres) in centre order.  Sites that are not medium (obstacle or
+    an earlier cube) are left alone.  Returns the number of cells placed."""
+    dim = lattice.ndim
+    lo = -(edge // 2)
+    offs = np.stack(np.meshgrid(*([np.arange(lo, lo + edge)] * dim), indexing="ij"),
+                    axis=-1).reshape(-1, dim)
+    n = 0
+    for cid, ctr in enumerate(centres, start=1):
+        pts = (ctr[None, :] + offs) % np.array(lattice.shape)[None, :]
+        idx = tuple(pts[:, d] for d in range(dim))
+        free = lattice[idx] == 0
+        lattice[tuple(p[free] for p in idx)] = cid
+        n = cid
+    return n
+
+
+# --------------------------------------------------------------------------
+# the workloads
+# --------------------------------------------------------------------------
+
+def config1_2d(seed: int = 1, n: int = 200, n_cells: int = 100, a: int = 4, c: int = 2,
+               P: int = 1, n_mcs: int = 500) -> Workload:
+    """2D CPM, n x n lattice, Moore-8, periodic; one-pixel cells at distinct
+    uniform random sites; target volume 100; J(cell,cell)=20,
+    J(cell,medium)=10, lambda_V=50, no perimeter or Act term, T=20 (S=1)."""
+    rng = np.random.default_rng(seed)
+    lat = np.zeros((1, n, n), dtype=np.int32)
+    sites = rng.choice(n * n, size=n_cells, replace=False)
+    lat.reshape(-1)[sites] = np.arange(1, n_cells + 1, dtype=np.int32)
+    J, lv, vt, lp, at, la, ma = _params()
+    _sym(J, 1, 1, 20)
+    _sym(J, 1, 0, 10)
+    lv[1] = 50
+    vt[1] = 100
+    ct = np.ones(n_cells + 1, dtype=np.uint8)
+    ct[0] = 0
+    return Workload("cpm2d_%dx%d_moore8_%dcells" % (n, n, n_cells), 2, n, n, 1, J, lv, vt, lp,
+                    at, la, ma, 20.0, 1, a, c, P, seed, 2, lat, ct, None, n_mcs)
+
+
+def config2_3d(seed: int = 1, n: int = 256, spacing: float = 10.0, a: int = 8, c: int = 2,
+               P: int = 2, n_mcs: int = 1000) -> Workload:
+    """3D CPM, n^3 lattice, 26-neighbourhood, periodic; 3^3 cubes at
+    blue-noise centres (jittered grid, spacing 10, jitter 2: about 16,000
+    cells at n=256); V_t=500, A_t=400; J(c,c)=20, J(c,m)=12, lambda_V=25,
+    lambda_P=0.5, T=20, all scaled by S=2."""
+    rng = np.random.default_rng(seed)
+    lat = np.zeros((n, n, n), dtype=np.int32)
+    ctr = jittered_centres((n, n, n), spacing, 2.0, rng)
+    ctr = ctr[rng.permutation(len(ctr))]
+    nc = place_cubes(lat, ctr, 3)
+    S = 2
+    J, lv, vt, lp, at, la, ma = _params()
+    _sym(J, 1, 1, 20 * S)
+    _sym(J, 1, 0, 12 * S)
+    lv[1] = 25 * S
+    vt[1] = 500
+    lp[1] = 1            # 0.5 * S
+    at[1] = 400
+    ct = np.ones(nc + 1, dtype=np.uint8)
+    ct[0] = 0
+    return Workload("cpm3d_%d^3_moore26_%dcells" % (n, nc), 3, n, n, n, J, lv, vt, lp, at,
+                    la, ma, 20.0 * S, S, a, c, P, seed, 2, lat, ct, None, n_mcs)
+
+
+# Target surface for config 3.  The paper gives none for this workload; it is
+# fixed at 1.2x the 26-neighbourhood interface count of a digital ball of about
+# 800 voxels (radius 5.75: 799 voxels, 3,866 interfaces), i.e. 4,639.
+CONFIG3_A_TARGET = 4639
+
+
+def fibre_mask(shape, rng, cell_spacing: float = 48.0, frac: float = 0.15,
+               device: Optional[str] = None) -> np.ndarray:
+    """Boolean mask of a Voronoi-edge 'fibre' network.
+
+    Voronoi seeds sit on a jittered grid of the given spacing; a voxel lies on
+    the network when its nearest and third-nearest seeds are almost equally
+    far (it is close to a line where three Voronoi regions meet).  The
+    closeness threshold is chosen as the ``frac`` quantile of that gap, so the
+    mask freezes ``frac`` of the voxels.  Periodic.  Uses torch (on ``device``
+    if given) only to evaluate distances quickly."""
+    import torch
+    dev = torch.device(device or "cpu")
+    shape = tuple(int(s) for s in shape)
+    g = [max(1, int(round(n / cell_spacing))) for n in shape]
+    step = [shape[d] / g[d] for d in range(3)]
+    jit = rng.uniform(-0.4, 0.4, size=(g[0], g[1], g[2], 3))
+    base = np.stack(np.meshgrid(*[np.arange(m) for m in g], indexing="ij"), axis=-1)
+    seeds = (base + 0.5 + jit) * np.array(step)[None, None, None, :]
+    seeds_t = torch.tensor(seeds, dtype=torch.float32, device=dev)
+    gz, gy, gx = g
+    nz, ny, nx = shape
+    out = np.zeros(shape, dtype=np.float32)
+    # candidate seeds: the 4x4x4 grid cells around each voxel's own cell
+    offs = torch.tensor([(i, j, k) for i in range(-2, 2) for j in range(-2, 2) for k in range(-2, 2)],
+                        device=dev)
+    L = torch.tensor([nz, ny, nx], dtype=torch.float32, device=dev)
+    yy, xx = torch.meshgrid(torch.arange(ny, device=dev), torch.arange(nx, device=dev), indexing="ij")
+    for z in range(nz):
+        p = torch.stack([torch.full_like(yy, z), yy, xx], dim=-1).float() + 0.5   # [ny, nx, 3]
+        cell = torch.stack([(p[..., d] / step[d]).floor().long() for d in range(3)], dim=-1)
+        frac_in = torch.stack([p[..., d] / step[d] - cell[..., d] for d in range(3)], dim=-1)
+        # choose the 4 cells along each axis so the voxel sits in the middle two
+        shift = (frac_in >= 0.5).long()
+        cand = cell[..., None, :] + offs[None, None, :, :] + shift[..., None, :]
+        ci = torch.stack([cand[..., d] % g[d] for d in range(3)], dim=-1)
+        sp = seeds_t[ci[..., 0], ci[..., 1], ci[..., 2]]      # [ny, nx, 64, 3]
+        d = sp - p[..., None, :]
+        d = d - torch.round(d / L) * L
+        dist = d.norm(dim=-1)
+        top = torch.topk(dist, 3, dim=-1, largest=False).values
+        out[z] = (top[..., 2] - top[..., 0]).cpu().numpy()
+    thr = np.quantile(out[:: max(1, nz // 64)], frac)
+    return out < thr
+
+
+def config3_3d(seed: int = 1, n: int = 1024, a: int = 8, c: int = 2, P: int = 2,
+               n_mcs: int = 200, device: Optional[str] = None,
+               fibre_spacing: float = 48.0) -> Workload:
+    """3D tissue-scale CPM with a frozen Voronoi-edge fibre network (about 15%
+    of voxels) and motile cells (Act model on).  Cells start as 3^3 cubes at
+    blue-noise centres (spacing 10) outside the fibres; V_t=800; Act:
+    lambda_act=200, Max_act=30; J(c,c)=20, J(c,medium)=10, J(c,fibre)=40,
+    lambda_V=25, lambda_P=0.2, T=20, all scaled by S=5."""
+    rng = np.random.default_rng(seed)
+    shape = (n, n, n)
+    fib = fibre_mask(shape, rng, cell_spacing=min(fibre_spacing, n / 2), device=device)
+    lat = np.zeros(shape, dtype=np.int32)
+    lat[fib] = -1
+    ctr = jittered_centres(shape, 10.0, 2.0, rng)
+    ok = ~fib[ctr[:, 0], ctr[:, 1], ctr[:, 2]]
+    ctr = ctr[ok]
+    ctr = ctr[rng.permutation(len(ctr))]
+    nc = place_cubes(lat, ctr, 3)
+    S = 5
+    J, lv, vt, lp, at, la, ma = _params()
+    _sym(J, 1, 1, 20 * S)
+    _sym(J, 1, 0, 10 * S)
+    _sym(J, 1, 2, 40 * S)
+    lv[1] = 25 * S
+    vt[1] = 800
+    lp[1] = 1            # 0.2 * S
+    at[1] = CONFIG3_A_TARGET
+    la[1] = 200 * S
+    ma[1] = 30
+    ct = np.ones(nc + 1, dtype=np.uint8)
+    ct[0] = 0
+    return Workload("cpm3d_tissue_%d^3_act_fibre_%dcells" % (n, nc), 3, n, n, n, J, lv, vt,
+                    lp, at, la, ma, 20.0 * S, S, a, c, P, seed, 2, lat, ct, None, n_mcs)
+
+
+def random_small(seed: int, dim: int = 2, n: int = 16, n_cells: int = 6, edge: int = 3,
+                 perimeter: bool = True, act: bool = False, obstacles: float = 0.0,
+                 a: Optional[int] = None, c: int = 2, P: int = 1, T: float = 20.0,
+                 n_types: int = 2) -> Workload:
+    """Small randomised lattices for unit tests: cubes (squares) of random
+    types at random centres, optional obstacle sites and Act values, and
+    random integer parameters of the magnitudes the paper's tables use."""
+    rng = np.random.default_rng(seed)
+    shape = (n,) * dim
+    lat = np.zeros(shape, dtype=np.int32)
+    if obstacles > 0:
+        lat[rng.random(shape) < obstacles] = -1
+    ctr = rng.integers(0, n, size=(n_cells, dim))
+    nc = place_cubes(lat, ctr, edge)
+    J, lv, vt, lp, at, la, ma = _params()
+    obstacle_type = n_types + 1
+    for t1 in range(0, obstacle_type + 1):
+        for t2 in range(t1, obstacle_type + 1):
+            if t1 == 0 and t2 == 0:
+                continue
+            _sym(J, t1, t2, int(rng.integers(0, 40)))
+    for t in range(1, n_types + 1):
+        lv[t] = int(rng.integers(1, 60))
+        vt[t] = int(rng.integers(4, max(5, 4 * edge ** dim)))
+        if perimeter:
+            lp[t] = int(rng.integers(1, 4))
+            at[t] = int(rng.integers(4, 8 * edge ** (dim - 1) * (3 if dim == 3 else 2)))
+        if act:
+            la[t] = int(rng.integers(50, 800))
+            ma[t] = int(rng.integers(5, 60))
+    ct = np.zeros(nc + 1, dtype=np.uint8)
+    ct[1:] = rng.integers(1, n_types + 1, size=nc)
+    actv = None
+    if act:
+        actv = np.zeros(shape, dtype=np.uint8)
+        cells = lat > 0
+        mx = ma[ct[np.maximum(lat, 0)]]
+        draw = rng.integers(0, 61, size=shape)
+        actv[cells] = np.minimum(draw[cells], mx[cells]).astype(np.uint8)
+    if a is None:
+        a = 4
+    if dim == 2:
+        lat = lat[None]
+        if actv is not None:
+            actv = actv[None]
+    nz = 1 if dim == 2 else n
+    return Workload("random_small_%dd_%d" % (dim, seed), dim, n, n, nz, J, lv, vt, lp, at, la,
+                    ma, float(T), 1, a, c, P, seed, obstacle_type, lat, ct, actv, 1)
