@@ -1,0 +1,169 @@
+/*
+ * cpm.h -- C ABI of the GB300 cellular Potts model (CPM) sweep library
+ * (libcpm_gb300.so).
+ *
+ * The library runs the parallel Metropolis copy-attempt sweep of the CPM
+ * (Sultan, Devi, Mueller, Textor, "A parallelized cellular Potts model that
+ * enables simulations at tissue scale", arXiv 2312.09317) on one GPU:
+ *
+ *   Hamiltonian     Methods, Eq. 1 (adhesion J over Moore-neighbour pairs,
+ *                   each unordered pair counted once; volume term) and Eq. 3
+ *                   (perimeter term, A = interfaces with other ids);
+ *   acceptance      Methods, Eq. 2: min(1, exp(-dH/T));
+ *   Act motility    Methods, Eq. 7 and Eq. 8 (geometric mean of Act over the
+ *                   site and its same-cell Moore neighbours; Act set to
+ *                   Max_act on update, decays by 1 per MCS);
+ *   parallel scheme Results, "Designing a parallel execution scheme" and
+ *                   "Aligning the lattice update statistics" (Fig. 2A/B,
+ *                   Fig. 3A/B): a checkerboard of blocks, atomic tally
+ *                   updates, a barrier after every copy attempt.
+ *
+ * Semantics fixed by this library (the paper leaves them open):
+ *   - The lattice is split into areas of edge a; each area into c^d blocks
+ *     of edge s = a/c; block (bx,by,bz) has colour (bx%c) + c(by%c) +
+ *     c^2(bz%c).  One MCS is P cycles; each cycle visits the c^d colours in
+ *     an order drawn from Philox; a visit (a "sub-pass") runs k = s^d/P
+ *     rounds; in a round every block of the active colour makes one copy
+ *     attempt into a target site of its own block from a uniformly chosen
+ *     Moore neighbour.  So each MCS makes exactly one attempt per site.
+ *   - All attempts of a round read the tallies (volume V, interface count A
+ *     per cell) as they stood when the round began; the round's own changes
+ *     become visible in the next round.  Blocks of one colour are >= 2 sites
+ *     apart (a - s >= 2), so their lattice reads and writes never overlap.
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed,
+ *     counter = (block index, round, MCS, sub-pass) for attempts (word 0
+ *     picks the target in the block, word 1 the neighbour, word 2 is the
+ *     acceptance draw) and (i, cycle, MCS, 1<<24) for the colour shuffle.
+ *   - Energies are integers (the caller scales J and the lambdas by an
+ *     integer S and passes T scaled by S); the Act term is added in Q4 fixed
+ *     point through integer tables; acceptance compares the uint32 draw with
+ *     THR[dH] = min(2^32-1, floor(2^32 exp(-dH/(16T)))).
+ *   - A copy that would remove a cell's last site is rejected.
+ *   The result is a deterministic function of (config, seed, number of
+ *   sub-passes run): cpm_step(h, a) then cpm_step(h, b) equals
+ *   cpm_step(h, a + b), on any GPU.
+ *
+ * Data conventions: lattice int32, x fastest (idx = x + nx*(y + ny*z));
+ * id 0 = medium (type 0, no tallies), ids 1..n_cells = cells, id -1 = frozen
+ * obstacle of type obstacle_type.  Boundaries are periodic.
+ *
+ * Ownership: the library allocates and owns every device buffer of a
+ * handle; pointers passed in are borrowed for the duration of the call.
+ * Host pointers must be readable/writable for the stated sizes; device
+ * pointers must be device memory of the handle's GPU.
+ *
+ * Errors: every int-returning call returns CPM_OK (0) or a negative
+ * CPM_E_* code and records a message readable with cpm_last_error.  No call
+ * aborts the process.  After CPM_E_CUDA the handle should be destroyed.
+ *
+ * Streams: all work of a handle is issued on the stream given to
+ * cpm_create (0 = the legacy default stream).  Calls that return data to the
+ * host synchronise that stream.
+ */
+#ifndef CPM_GB300_H
+#define CPM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CPM_MAX_TYPES 8
+
+enum {
+    CPM_OK = 0,
+    CPM_E_INVALID = -1,   /* bad argument or configuration */
+    CPM_E_NOMEM = -2,     /* device or host allocation failed */
+    CPM_E_CUDA = -3,      /* a CUDA runtime call failed */
+    CPM_E_HANDLE = -4,    /* NULL or destroyed handle */
+    CPM_E_STATE = -5      /* device-side consistency check failed */
+};
+
+typedef struct cpm_config {
+    int32_t dim;                 /* 2 or 3 */
+    int32_t nx, ny, nz;          /* extents; nz = 1 when dim = 2; multiples of a */
+    int32_t J[CPM_MAX_TYPES][CPM_MAX_TYPES];   /* adhesion, symmetric, scaled */
+    int32_t lambda_v[CPM_MAX_TYPES];           /* volume weight per type, scaled */
+    int32_t v_target[CPM_MAX_TYPES];
+    int32_t lambda_p[CPM_MAX_TYPES];           /* perimeter weight, scaled */
+    int32_t a_target[CPM_MAX_TYPES];
+    int32_t lambda_act[CPM_MAX_TYPES];         /* Act weight, scaled (all 0: Act off) */
+    int32_t max_act[CPM_MAX_TYPES];            /* Max_act, 0..127 */
+    double temperature;          /* T in the same scaled energy units, > 0 */
+    int32_t obstacle_type;       /* type of id -1 sites, 1..CPM_MAX_TYPES-1 */
+    int32_t a, c, P;             /* area edge, divisions per axis, cycles per MCS */
+    uint64_t seed;
+    int32_t n_cells;             /* cells have ids 1..n_cells */
+    const uint8_t *cell_type;    /* host, n_cells + 1 entries; [0] must be 0 */
+    const int32_t *init_lattice; /* host, nx*ny*nz ids in -1..n_cells */
+    const uint8_t *init_act;     /* host, nx*ny*nz Act values or NULL (all 0) */
+    int64_t t0;                  /* MCS index of the first MCS to run (>= 0) */
+} cpm_config;
+
+typedef struct cpm_stats_t {
+    int64_t mcs;            /* MCS index of the next sub-pass (completed MCS if sp == 0) */
+    int32_t subpass;        /* next sub-pass within that MCS */
+    int32_t n_live_cells;   /* cells with V > 0 */
+    int64_t attempts;       /* copy attempts made by this handle */
+    int64_t accepts;        /* accepted copies made by this handle */
+    double volume_mean, volume_var;        /* over live cells */
+    double perimeter_mean, perimeter_var;  /* over live cells */
+} cpm_stats_t;
+
+typedef struct cpm_handle cpm_handle;
+
+/* Validate cfg, allocate device state, upload the initial lattice, compute
+ * the tallies and the threshold/log/exp tables.  cuda_stream is a
+ * cudaStream_t (or NULL).  On success *out receives a handle.
+ * Errors: CPM_E_INVALID (message says which field), CPM_E_NOMEM, CPM_E_CUDA. */
+int cpm_create(const cpm_config *cfg, void *cuda_stream, cpm_handle **out);
+
+/* Run n_mcs Monte Carlo steps (n_mcs * P * c^d sub-passes).  Asynchronous on
+ * the handle's stream.  n_mcs >= 0. */
+int cpm_step(cpm_handle *h, int64_t n_mcs);
+
+/* Run n sub-passes (colour visits); cpm_step(h, m) = cpm_step_subpasses(h,
+ * m * P * c^d).  Used for finer-grained checks.  n >= 0. */
+int cpm_step_subpasses(cpm_handle *h, int64_t n);
+
+/* Copy the lattice (nx*ny*nz int32) to dst (host if dst_is_device == 0,
+ * device otherwise).  Synchronises the handle's stream. */
+int cpm_read_lattice(cpm_handle *h, int32_t *dst, int dst_is_device);
+
+/* Copy the tallies: V and A, n_cells + 1 int32 each (entry 0 unused, 0).
+ * Either pointer may be NULL.  Synchronises the stream. */
+int cpm_read_tallies(cpm_handle *h, int32_t *V, int32_t *A, int dst_is_device);
+
+/* Copy the Act values (nx*ny*nz uint8) as seen after the last completed
+ * sub-pass (all 0 when Act is off).  Synchronises the stream. */
+int cpm_read_act(cpm_handle *h, uint8_t *dst, int dst_is_device);
+
+/* Replace the lattice with src (host or device, nx*ny*nz int32 in
+ * -1..n_cells; obstacle sites must stay where they are) and recompute the
+ * tallies on the device.  Act values and the position are kept. */
+int cpm_load_lattice(cpm_handle *h, const int32_t *src, int src_is_device);
+
+/* Counters and moments of the tallies.  Synchronises the stream. */
+int cpm_stats(cpm_handle *h, cpm_stats_t *out);
+
+/* Recount V and A from the lattice on the device and compare with the
+ * tallies; *n_mismatch receives the number of cells that differ (0 when the
+ * bookkeeping is exact).  Synchronises the stream. */
+int cpm_verify(cpm_handle *h, int64_t *n_mismatch);
+
+/* Number of kernel launches the library has issued for this handle. */
+int64_t cpm_kernel_launches(const cpm_handle *h);
+
+/* Message of the last failed call on h (or of the last failed cpm_create
+ * when h is NULL).  The string stays valid until the next call on h. */
+const char *cpm_last_error(const cpm_handle *h);
+
+/* Free every resource of h (NULL is ignored).  Synchronises the stream. */
+void cpm_destroy(cpm_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPM_GB300_H */

@@ -1,0 +1,215 @@
+"""Python binding of the C ABI in include/cpm.h (libcpm_gb300.so).
+
+Argument marshalling only: every step of the sweep runs in the library's CUDA
+kernels.  Device buffers may be passed as torch CUDA tensors (their data
+pointers are handed over), host buffers as numpy arrays.  The library must
+have been built (``paper_2312_09317_gb300.build.build()``); importing this
+module without it raises, so nothing silently falls back to another path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAX_TYPES = 8
+
+CPM_OK, CPM_E_INVALID, CPM_E_NOMEM, CPM_E_CUDA, CPM_E_HANDLE, CPM_E_STATE = 0, -1, -2, -3, -4, -5
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("J", (ctypes.c_int32 * MAX_TYPES) * MAX_TYPES),
+        ("lambda_v", ctypes.c_int32 * MAX_TYPES), ("v_target", ctypes.c_int32 * MAX_TYPES),
+        ("lambda_p", ctypes.c_int32 * MAX_TYPES), ("a_target", ctypes.c_int32 * MAX_TYPES),
+        ("lambda_act", ctypes.c_int32 * MAX_TYPES), ("max_act", ctypes.c_int32 * MAX_TYPES),
+        ("temperature", ctypes.c_double),
+        ("obstacle_type", ctypes.c_int32),
+        ("a", ctypes.c_int32), ("c", ctypes.c_int32), ("P", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("n_cells", ctypes.c_int32),
+        ("cell_type", ctypes.POINTER(ctypes.c_uint8)),
+        ("init_lattice", ctypes.POINTER(ctypes.c_int32)),
+        ("init_act", ctypes.POINTER(ctypes.c_uint8)),
+        ("t0", ctypes.c_int64),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("mcs", ctypes.c_int64), ("subpass", ctypes.c_int32), ("n_live_cells", ctypes.c_int32),
+        ("attempts", ctypes.c_int64), ("accepts", ctypes.c_int64),
+        ("volume_mean", ctypes.c_double), ("volume_var", ctypes.c_double),
+        ("perimeter_mean", ctypes.c_double), ("perimeter_var", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# Every function the header declares, with its ctypes signature.
+_SIGNATURES = {
+    "cpm_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "cpm_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "cpm_step_subpasses": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "cpm_read_lattice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "cpm_read_tallies": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "cpm_read_act": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "cpm_load_lattice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "cpm_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
+    "cpm_verify": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "cpm_kernel_launches": (ctypes.c_int64, [ctypes.c_void_p]),
+    "cpm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "cpm_destroy": (None, [ctypes.c_void_p]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libcpm_gb300.so (raises OSError/RuntimeError when it is absent)."""
+    global _lib
+    if _lib is None:
+        p = path or library_path()
+        if not os.path.exists(p):
+            raise RuntimeError("libcpm_gb300.so is not built (%s); run __graft_entry__.build()" % p)
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class CPMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("CPM error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _ptr(x):
+    """Data pointer and is-device flag of a numpy array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data, 0
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr(), 1 if x.is_cuda else 0
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def make_config(w, keep: list) -> Config:
+    """Config for a cpm_workloads.Workload; arrays it points to are appended
+    to ``keep`` so they outlive the call."""
+    c = Config()
+    c.dim, c.nx, c.ny, c.nz = w.dim, w.nx, w.ny, w.nz
+    for a in range(MAX_TYPES):
+        for b in range(MAX_TYPES):
+            c.J[a][b] = int(w.J[a, b])
+        c.lambda_v[a] = int(w.lambda_v[a])
+        c.v_target[a] = int(w.v_target[a])
+        c.lambda_p[a] = int(w.lambda_p[a])
+        c.a_target[a] = int(w.a_target[a])
+        c.lambda_act[a] = int(w.lambda_act[a])
+        c.max_act[a] = int(w.max_act[a])
+    c.temperature = float(w.T)
+    c.obstacle_type = int(w.obstacle_type)
+    c.a, c.c, c.P = w.a, w.c, w.P
+    c.seed = int(w.seed)
+    c.n_cells = int(w.n_cells)
+    ct = np.ascontiguousarray(w.cell_type, dtype=np.uint8)
+    lat = np.ascontiguousarray(w.lattice, dtype=np.int32)
+    keep += [ct, lat]
+    c.cell_type = ct.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    c.init_lattice = lat.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    if w.act is not None:
+        act = np.ascontiguousarray(w.act, dtype=np.uint8)
+        keep.append(act)
+        c.init_act = act.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    c.t0 = 0
+    return c
+
+
+class Sim:
+    """One CPM lattice on the GPU (a cpm_handle)."""
+
+    def __init__(self, w, stream=None):
+        lib = load()
+        keep: list = []
+        cfg = make_config(w, keep)
+        self.w = w
+        h = ctypes.c_void_p()
+        st = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+        rc = lib.cpm_create(ctypes.byref(cfg), ctypes.c_void_p(st), ctypes.byref(h))
+        if rc != CPM_OK:
+            raise CPMError(rc, lib.cpm_last_error(None).decode())
+        self.h = h
+        self.lib = lib
+
+    def _check(self, rc):
+        if rc != CPM_OK:
+            raise CPMError(rc, self.lib.cpm_last_error(self.h).decode())
+
+    def step(self, n_mcs: int = 1):
+        self._check(self.lib.cpm_step(self.h, n_mcs))
+
+    def step_subpasses(self, n: int):
+        self._check(self.lib.cpm_step_subpasses(self.h, n))
+
+    def read_lattice(self, out=None):
+        if out is None:
+            out = np.empty((self.w.nz, self.w.ny, self.w.nx), dtype=np.int32)
+        p, dev = _ptr(out)
+        self._check(self.lib.cpm_read_lattice(self.h, ctypes.c_void_p(p), dev))
+        return out
+
+    def read_tallies(self):
+        V = np.empty(self.w.n_cells + 1, dtype=np.int32)
+        A = np.empty(self.w.n_cells + 1, dtype=np.int32)
+        self._check(self.lib.cpm_read_tallies(self.h, ctypes.c_void_p(V.ctypes.data),
+                                              ctypes.c_void_p(A.ctypes.data), 0))
+        return V, A
+
+    def read_act(self, out=None):
+        if out is None:
+            out = np.empty((self.w.nz, self.w.ny, self.w.nx), dtype=np.uint8)
+        p, dev = _ptr(out)
+        self._check(self.lib.cpm_read_act(self.h, ctypes.c_void_p(p), dev))
+        return out
+
+    def load_lattice(self, src):
+        p, dev = _ptr(src)
+        self._check(self.lib.cpm_load_lattice(self.h, ctypes.c_void_p(p), dev))
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(self.lib.cpm_stats(self.h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def verify(self) -> int:
+        n = ctypes.c_int64(0)
+        self._check(self.lib.cpm_verify(self.h, ctypes.byref(n)))
+        return n.value
+
+    def launches(self) -> int:
+        return int(self.lib.cpm_kernel_launches(self.h))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.cpm_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,490 @@
+// Host side of the C ABI declared in include/cpm.h: configuration checks,
+// device state, the integer tables, the colour schedule and the launch loop.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/cpm.h"
+#include "cpm_internal.h"
+
+using namespace cpmgb;
+
+struct cpm_handle {
+    cpm_config cfg;  // pointers inside are not kept
+    TypeParams tp;
+    cudaStream_t stream = nullptr;
+    int dim = 2, nb = 8;
+    uint64_t n_sites = 0;
+    int32_t n_cells = 0;
+    uint32_t s = 1, C = 1, sd = 1, k = 1, per_mcs = 1;
+    uint32_t nbx = 1, nby = 1, nbz = 1, n_active = 0;
+    bool perim = false, act = false;
+    // device state
+    int32_t *lat = nullptr;
+    uint8_t *stamp = nullptr;
+    uint8_t *cell_type = nullptr;
+    int32_t *tallies = nullptr;  // V0, A0, V1, A1, Vtmp, Atmp; each n_cells + 1
+    int4 *pend = nullptr;        // two buffers of n_active
+    uint32_t *thr = nullptr;
+    int32_t *ln_tab = nullptr;
+    int32_t *expq = nullptr;
+    unsigned long long *counters = nullptr;  // [0] accepts, [1] scratch
+    uint8_t *act_tmp = nullptr;
+    int32_t L = 0;
+    // position
+    int64_t t = 0;
+    int32_t sp = 0;
+    uint64_t g = 0;  // global round index
+    int64_t launches = 0;
+    int64_t attempts = 0;
+    std::string err;
+};
+
+namespace {
+
+std::string g_create_error;
+
+int fail(cpm_handle *h, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf; else g_create_error = buf;
+    return code;
+}
+
+#define CUDA_TRY(h, expr)                                                                        \
+    do {                                                                                         \
+        cudaError_t e_ = (expr);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail((h), e_ == cudaErrorMemoryAllocation ? CPM_E_NOMEM : CPM_E_CUDA, "%s: %s", \
+                        #expr, cudaGetErrorString(e_));                                          \
+    } while (0)
+
+uint32_t ipow(uint32_t b, int e)
+{
+    uint32_t r = 1;
+    while (e-- > 0) r *= b;
+    return r;
+}
+
+int32_t *V_buf(cpm_handle *h, int which) { return h->tallies + (size_t)(2 * which) * (h->n_cells + 1); }
+int32_t *A_buf(cpm_handle *h, int which) { return h->tallies + (size_t)(2 * which + 1) * (h->n_cells + 1); }
+
+int validate(const cpm_config *c)
+{
+    if (!c) return fail(nullptr, CPM_E_INVALID, "cfg is NULL");
+    if (c->dim != 2 && c->dim != 3) return fail(nullptr, CPM_E_INVALID, "dim must be 2 or 3");
+    if (c->nx < 3 || c->ny < 3 || (c->dim == 3 && c->nz < 3) || (c->dim == 2 && c->nz != 1))
+        return fail(nullptr, CPM_E_INVALID, "extents must be >= 3 (nz = 1 in 2D)");
+    const uint64_t n = (uint64_t)c->nx * c->ny * c->nz;
+    if (n > (1ull << 31)) return fail(nullptr, CPM_E_INVALID, "at most 2^31 sites");
+    if (c->c < 2 || c->a < 2 || c->a % c->c) return fail(nullptr, CPM_E_INVALID, "need c >= 2 and c | a");
+    const int s = c->a / c->c;
+    if (c->a - s < 2) return fail(nullptr, CPM_E_INVALID, "blocks of one colour must be >= 2 sites apart (a - a/c >= 2)");
+    if (c->nx % c->a || c->ny % c->a || (c->dim == 3 && c->nz % c->a))
+        return fail(nullptr, CPM_E_INVALID, "extents must be multiples of a");
+    if (ipow(c->c, c->dim) > 27) return fail(nullptr, CPM_E_INVALID, "at most 27 colours");
+    const uint32_t sd = ipow(s, c->dim);
+    if (c->P < 1 || sd % c->P) return fail(nullptr, CPM_E_INVALID, "P must divide s^d");
+    if (!(c->temperature > 0.0) || c->temperature > 2900.0)
+        return fail(nullptr, CPM_E_INVALID, "temperature must be in (0, 2900]");
+    if (c->obstacle_type < 1 || c->obstacle_type >= CPM_MAX_TYPES) return fail(nullptr, CPM_E_INVALID, "bad obstacle_type");
+    if (c->n_cells < 0 || c->n_cells > (1 << 30)) return fail(nullptr, CPM_E_INVALID, "bad n_cells");
+    if (!c->cell_type || !c->init_lattice) return fail(nullptr, CPM_E_INVALID, "cell_type and init_lattice are required");
+    if (c->cell_type[0] != 0) return fail(nullptr, CPM_E_INVALID, "cell_type[0] (medium) must be 0");
+    for (int i = 1; i <= c->n_cells; i++)
+        if (c->cell_type[i] < 1 || c->cell_type[i] >= CPM_MAX_TYPES)
+            return fail(nullptr, CPM_E_INVALID, "cell_type[%d] out of range", i);
+    for (int a = 0; a < CPM_MAX_TYPES; a++) {
+        for (int b = 0; b < CPM_MAX_TYPES; b++)
+            if (c->J[a][b] != c->J[b][a]) return fail(nullptr, CPM_E_INVALID, "J must be symmetric");
+        if (c->max_act[a] < 0 || c->max_act[a] > 127) return fail(nullptr, CPM_E_INVALID, "max_act must be in 0..127");
+        if (c->lambda_v[a] < 0 || c->lambda_p[a] < 0 || c->lambda_act[a] < 0)
+            return fail(nullptr, CPM_E_INVALID, "lambdas must be >= 0");
+    }
+    if (c->t0 < 0) return fail(nullptr, CPM_E_INVALID, "t0 must be >= 0");
+    for (uint64_t x = 0; x < n; x++) {
+        const int32_t v = c->init_lattice[x];
+        if (v < -1 || v > c->n_cells) return fail(nullptr, CPM_E_INVALID, "init_lattice[%llu] = %d out of range",
+                                                  (unsigned long long)x, v);
+        if (c->init_act && c->init_act[x]) {
+            if (v <= 0) return fail(nullptr, CPM_E_INVALID, "init_act must be 0 outside cells");
+            if (c->init_act[x] > c->max_act[c->cell_type[v]])
+                return fail(nullptr, CPM_E_INVALID, "init_act above max_act at site %llu", (unsigned long long)x);
+        }
+    }
+    return CPM_OK;
+}
+
+// Colour visited at sub-pass sp of MCS t: a Fisher-Yates shuffle of the C
+// colours per cycle, swap i (C-1 down to 1) drawn from counter (i, cycle, t, 1<<24).
+uint32_t colour_of(const cpm_handle *h, int64_t t, int32_t sp)
+{
+    uint32_t perm[27];
+    for (uint32_t q = 0; q < h->C; q++) perm[q] = q;
+    const uint32_t cycle = (uint32_t)sp / h->C;
+    for (uint32_t i = h->C - 1; i >= 1; i--) {
+        const Philox4 w = philox4x32_10(i, cycle, (uint32_t)t, 1u << 24, (uint32_t)h->cfg.seed,
+                                        (uint32_t)(h->cfg.seed >> 32));
+        const uint32_t j = draw_below(w.v[0], i + 1);
+        const uint32_t tmp = perm[i];
+        perm[i] = perm[j];
+        perm[j] = tmp;
+    }
+    return perm[(uint32_t)sp % h->C];
+}
+
+int recount(cpm_handle *h, int32_t *V, int32_t *A)
+{
+    const size_t bytes = sizeof(int32_t) * (h->n_cells + 1);
+    CUDA_TRY(h, cudaMemsetAsync(V, 0, bytes, h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(A, 0, bytes, h->stream));
+    CUDA_TRY(h, launch_recount(h->dim, h->lat, h->cell_type, V, A, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->stream));
+    h->launches += 1;
+    return CPM_OK;
+}
+
+// Recompute the tallies from the lattice into both buffers and forget pending changes.
+int reset_tallies(cpm_handle *h)
+{
+    const int cur = (int)(h->g & 1);
+    int rc = recount(h, V_buf(h, cur), A_buf(h, cur));
+    if (rc) return rc;
+    const size_t bytes = sizeof(int32_t) * (h->n_cells + 1);
+    CUDA_TRY(h, cudaMemcpyAsync(V_buf(h, cur ^ 1), V_buf(h, cur), bytes, cudaMemcpyDeviceToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(A_buf(h, cur ^ 1), A_buf(h, cur), bytes, cudaMemcpyDeviceToDevice, h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(h->pend, 0, sizeof(int4) * 2 * (size_t)h->n_active, h->stream));
+    return CPM_OK;
+}
+
+int run_subpass(cpm_handle *h)
+{
+    if (h->act && h->sp == 0 && h->t % 64 == 0) {
+        CUDA_TRY(h, launch_clamp_stamps(h->stamp, h->n_sites, (uint32_t)h->t, h->stream));
+        h->launches += 1;
+    }
+    const uint32_t col = colour_of(h, h->t, h->sp);
+    RoundArgs a;
+    memset(&a, 0, sizeof a);
+    a.lat = h->lat;
+    a.stamp = h->stamp;
+    a.cell_type = h->cell_type;
+    a.thr = h->thr;
+    a.ln_tab = h->ln_tab;
+    a.expq = h->expq;
+    a.accepts = h->counters;
+    a.L = h->L;
+    a.nx = h->cfg.nx; a.ny = h->cfg.ny; a.nz = h->cfg.nz;
+    a.s = h->s; a.c = h->cfg.c; a.sd = h->sd;
+    a.nbx = h->nbx; a.nby = h->nby;
+    a.nax = h->nbx / h->cfg.c; a.nay = h->nby / h->cfg.c;
+    a.n_active = h->n_active;
+    a.cx = col % h->cfg.c;
+    a.cy = (col / h->cfg.c) % h->cfg.c;
+    a.cz = col / (h->cfg.c * h->cfg.c);
+    a.t = (uint32_t)h->t;
+    a.sp = (uint32_t)h->sp;
+    a.key0 = (uint32_t)h->cfg.seed;
+    a.key1 = (uint32_t)(h->cfg.seed >> 32);
+    a.tp = h->tp;
+    for (uint32_t r = 0; r < h->k; r++) {
+        const int cur = (int)(h->g & 1);
+        a.r = r;
+        a.Vc = V_buf(h, cur);
+        a.Ac = A_buf(h, cur);
+        a.Vn = V_buf(h, cur ^ 1);
+        a.An = A_buf(h, cur ^ 1);
+        a.pend_prev = h->pend + (size_t)(cur ^ 1) * h->n_active;
+        a.pend_cur = h->pend + (size_t)cur * h->n_active;
+        CUDA_TRY(h, launch_round(h->dim, h->perim, h->act, a, h->stream));
+        h->launches += 1;
+        h->g += 1;
+        h->attempts += h->n_active;
+    }
+    if (++h->sp == (int32_t)h->per_mcs) {
+        h->sp = 0;
+        h->t += 1;
+    }
+    return CPM_OK;
+}
+
+int build_tables(cpm_handle *h)
+{
+    // THR[h] = min(2^32-1, floor(2^32 exp(-h/(16T)))) up to the first zero
+    std::vector<uint32_t> thr;
+    const double T = h->cfg.temperature;
+    for (int64_t e = 0;; e++) {
+        const double v = std::floor(std::ldexp(std::exp(-(double)e / (16.0 * T)), 32));
+        if (v <= 0.0) break;
+        thr.push_back(v >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)v);
+        if (thr.size() > (1u << 22)) return fail(h, CPM_E_INVALID, "threshold table too long");
+    }
+    h->L = (int32_t)thr.size();
+    // LN[a] = round(2^16 ln a), EXPQ[m] = round(2^16 exp(m/1024))
+    std::vector<int32_t> ln(kLnEntries, 0);
+    for (int a = 1; a < kLnEntries; a++) ln[a] = (int32_t)std::llround(std::ldexp(std::log((double)a), 16));
+    const int32_t ne = (ln[kLnEntries - 1] >> 6) + 1;
+    std::vector<int32_t> ex(ne);
+    for (int m = 0; m < ne; m++) ex[m] = (int32_t)std::llround(std::ldexp(std::exp((double)m / 1024.0), 16));
+    CUDA_TRY(h, cudaMalloc(&h->thr, sizeof(uint32_t) * thr.size()));
+    CUDA_TRY(h, cudaMalloc(&h->ln_tab, sizeof(int32_t) * ln.size()));
+    CUDA_TRY(h, cudaMalloc(&h->expq, sizeof(int32_t) * ex.size()));
+    CUDA_TRY(h, cudaMemcpyAsync(h->thr, thr.data(), sizeof(uint32_t) * thr.size(), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(h->ln_tab, ln.data(), sizeof(int32_t) * ln.size(), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(h->expq, ex.data(), sizeof(int32_t) * ex.size(), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return CPM_OK;
+}
+
+void free_all(cpm_handle *h)
+{
+    cudaFree(h->lat);
+    cudaFree(h->stamp);
+    cudaFree(h->cell_type);
+    cudaFree(h->tallies);
+    cudaFree(h->pend);
+    cudaFree(h->thr);
+    cudaFree(h->ln_tab);
+    cudaFree(h->expq);
+    cudaFree(h->counters);
+    cudaFree(h->act_tmp);
+}
+
+int create_impl(cpm_handle *h, const cpm_config *c)
+{
+    h->cfg = *c;
+    h->cfg.cell_type = nullptr;
+    h->cfg.init_lattice = nullptr;
+    h->cfg.init_act = nullptr;
+    h->dim = c->dim;
+    h->nb = c->dim == 3 ? 26 : 8;
+    h->n_sites = (uint64_t)c->nx * c->ny * c->nz;
+    h->n_cells = c->n_cells;
+    h->s = (uint32_t)(c->a / c->c);
+    h->C = ipow(c->c, c->dim);
+    h->sd = ipow(h->s, c->dim);
+    h->k = h->sd / c->P;
+    h->per_mcs = (uint32_t)c->P * h->C;
+    h->nbx = c->nx / h->s;
+    h->nby = c->ny / h->s;
+    h->nbz = c->dim == 3 ? c->nz / h->s : 1;
+    h->n_active = (uint32_t)((uint64_t)h->nbx * h->nby * h->nbz / h->C);
+    memcpy(h->tp.J, c->J, sizeof h->tp.J);
+    memcpy(h->tp.lambda_v, c->lambda_v, sizeof h->tp.lambda_v);
+    memcpy(h->tp.v_target, c->v_target, sizeof h->tp.v_target);
+    memcpy(h->tp.lambda_p, c->lambda_p, sizeof h->tp.lambda_p);
+    memcpy(h->tp.a_target, c->a_target, sizeof h->tp.a_target);
+    memcpy(h->tp.lambda_act, c->lambda_act, sizeof h->tp.lambda_act);
+    memcpy(h->tp.max_act, c->max_act, sizeof h->tp.max_act);
+    h->tp.obstacle_type = c->obstacle_type;
+    for (int a = 0; a < CPM_MAX_TYPES; a++) {
+        if (c->lambda_p[a]) h->perim = true;
+        if (c->lambda_act[a]) h->act = true;
+    }
+    h->t = c->t0;
+    h->sp = 0;
+    h->g = 0;
+
+    const size_t nv = (size_t)h->n_cells + 1;
+    CUDA_TRY(h, cudaMalloc(&h->lat, sizeof(int32_t) * h->n_sites));
+    CUDA_TRY(h, cudaMalloc(&h->cell_type, nv));
+    CUDA_TRY(h, cudaMalloc(&h->tallies, sizeof(int32_t) * nv * 6));
+    CUDA_TRY(h, cudaMalloc(&h->pend, sizeof(int4) * 2 * (size_t)h->n_active));
+    CUDA_TRY(h, cudaMalloc(&h->counters, sizeof(unsigned long long) * 2));
+    CUDA_TRY(h, cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * 2, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(h->lat, c->init_lattice, sizeof(int32_t) * h->n_sites, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(h->cell_type, c->cell_type, nv, cudaMemcpyHostToDevice, h->stream));
+    if (h->act) {
+        // stamps for the Act values as seen after MCS t0-1: age Max - act, or 128 (no activity)
+        std::vector<uint8_t> st(h->n_sites);
+        const int64_t tl = c->t0 - 1;
+        for (uint64_t x = 0; x < h->n_sites; x++) {
+            const int32_t v = c->init_lattice[x];
+            const int a = c->init_act ? c->init_act[x] : 0;
+            if (v > 0 && a > 0)
+                st[x] = (uint8_t)((tl - (c->max_act[c->cell_type[v]] - a)) & 255);
+            else
+                st[x] = (uint8_t)((c->t0 - 128) & 255);
+        }
+        CUDA_TRY(h, cudaMalloc(&h->stamp, h->n_sites));
+        CUDA_TRY(h, cudaMemcpyAsync(h->stamp, st.data(), h->n_sites, cudaMemcpyHostToDevice, h->stream));
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    }
+    int rc = build_tables(h);
+    if (rc) return rc;
+    rc = reset_tallies(h);
+    if (rc) return rc;
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return CPM_OK;
+}
+
+bool bad(const cpm_handle *h) { return h == nullptr; }
+
+}  // namespace
+
+extern "C" {
+
+int cpm_create(const cpm_config *cfg, void *cuda_stream, cpm_handle **out)
+{
+    if (!out) return fail(nullptr, CPM_E_INVALID, "out is NULL");
+    *out = nullptr;
+    int rc = validate(cfg);
+    if (rc) return rc;
+    cpm_handle *h = new (std::nothrow) cpm_handle();
+    if (!h) return fail(nullptr, CPM_E_NOMEM, "host allocation failed");
+    h->stream = (cudaStream_t)cuda_stream;
+    rc = create_impl(h, cfg);
+    if (rc) {
+        g_create_error = h->err;
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return CPM_OK;
+}
+
+int cpm_step_subpasses(cpm_handle *h, int64_t n)
+{
+    if (bad(h)) return CPM_E_HANDLE;
+    if (n < 0) return fail(h, CPM_E_INVALID, "n must be >= 0");
+    for (int64_t i = 0; i < n; i++) {
+        int rc = run_subpass(h);
+        if (rc) return rc;
+    }
+    return CPM_OK;
+}
+
+int cpm_step(cpm_handle *h, int64_t n_mcs)
+{
+    if (bad(h)) return CPM_E_HANDLE;
+    if (n_mcs < 0) return fail(h, CPM_E_INVALID, "n_mcs must be >= 0");
+    return cpm_step_subpasses(h, n_mcs * (int64_t)h->per_mcs);
+}
+
+int cpm_read_lattice(cpm_handle *h, int32_t *dst, int dst_is_device)
+{
+    if (bad(h)) return CPM_E_HANDLE;
+    if (!dst) return fail(h, CPM_E_INVALID, "dst is NULL");
+    CUDA_TRY(h, cudaMemcpyAsync(dst, h->lat, sizeof(int32_t) * h->n_sites,
+                                dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return CPM_OK;
+}
+
+int cpm_read_tallies(cpm_handle *h, int32_t *V, int32_t *A, int dst_is_device)
+{
+    if (bad(h)) return CPM_E_HANDLE;
+    const int cur = (int)(h->g & 1);
+    const size_t bytes = sizeof(int32_t) * (h->n_cells + 1);
+    const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (V) CUDA_TRY(h, cudaMemcpyAsync(V, V_buf(h, cur), bytes, kind, h->stream));
+    if (A) CUDA_TRY(h, cudaMemcpyAsync(A, A_buf(h, cur), bytes, kind, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return CPM_OK;
+}
+
+int cpm_read_act(cpm_handle *h, uint8_t *dst, int dst_is_device)
+{
+    if (bad(h)) return CPM_E_HANDLE;
+    if (!dst) return fail(h, CPM_E_INVALID, "dst is NULL");
+    const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (!h->act) {
+        if (dst_is_device)
+            CUDA_TRY(h, cudaMemsetAsync(dst, 0, h->n_sites, h->stream));
+        else
+            memset(dst, 0, h->n_sites);
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        return CPM_OK;
+    }
+    if (!h->act_tmp) CUDA_TRY(h, cudaMalloc(&h->act_tmp, h->n_sites));
+    const int64_t t_last = h->sp == 0 ? h->t - 1 : h->t;
+    CUDA_TRY(h, launch_act_values(h->lat, h->stamp, h->cell_type, h->tp, h->n_sites, (uint32_t)t_last, h->act_tmp,
+                                  h->stream));
+    h->launches += 1;
+    CUDA_TRY(h, cudaMemcpyAsync(dst, h->act_tmp, h->n_sites, kind, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return CPM_OK;
+}
+
+int cpm_load_lattice(cpm_handle *h, const int32_t *src, int src_is_device)
+{
+    if (bad(h)) return CPM_E_HANDLE;
+    if (!src) return fail(h, CPM_E_INVALID, "src is NULL");
+    CUDA_TRY(h, cudaMemcpyAsync(h->lat, src, sizeof(int32_t) * h->n_sites,
+                                src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    return reset_tallies(h);
+}
+
+int cpm_stats(cpm_handle *h, cpm_stats_t *out)
+{
+    if (bad(h)) return CPM_E_HANDLE;
+    if (!out) return fail(h, CPM_E_INVALID, "out is NULL");
+    std::vector<int32_t> V(h->n_cells + 1), A(h->n_cells + 1);
+    int rc = cpm_read_tallies(h, V.data(), A.data(), 0);
+    if (rc) return rc;
+    unsigned long long acc = 0;
+    CUDA_TRY(h, cudaMemcpy(&acc, h->counters, sizeof acc, cudaMemcpyDeviceToHost));
+    double sv = 0, sv2 = 0, sa = 0, sa2 = 0;
+    int32_t live = 0;
+    for (int32_t i = 1; i <= h->n_cells; i++) {
+        if (V[i] <= 0) continue;
+        live++;
+        sv += V[i];
+        sv2 += (double)V[i] * V[i];
+        sa += A[i];
+        sa2 += (double)A[i] * A[i];
+    }
+    memset(out, 0, sizeof *out);
+    out->mcs = h->t;
+    out->subpass = h->sp;
+    out->n_live_cells = live;
+    out->attempts = h->attempts;
+    out->accepts = (int64_t)acc;
+    if (live > 0) {
+        out->volume_mean = sv / live;
+        out->volume_var = sv2 / live - out->volume_mean * out->volume_mean;
+        out->perimeter_mean = sa / live;
+        out->perimeter_var = sa2 / live - out->perimeter_mean * out->perimeter_mean;
+    }
+    return CPM_OK;
+}
+
+int cpm_verify(cpm_handle *h, int64_t *n_mismatch)
+{
+    if (bad(h)) return CPM_E_HANDLE;
+    if (!n_mismatch) return fail(h, CPM_E_INVALID, "n_mismatch is NULL");
+    int rc = recount(h, V_buf(h, 2), A_buf(h, 2));
+    if (rc) return rc;
+    const int cur = (int)(h->g & 1);
+    CUDA_TRY(h, cudaMemsetAsync(h->counters + 1, 0, sizeof(unsigned long long), h->stream));
+    CUDA_TRY(h, launch_compare(V_buf(h, cur), A_buf(h, cur), V_buf(h, 2), A_buf(h, 2), h->n_cells + 1,
+                               h->counters + 1, h->stream));
+    h->launches += 1;
+    unsigned long long bad_cells = 0;
+    CUDA_TRY(h, cudaMemcpyAsync(&bad_cells, h->counters + 1, sizeof bad_cells, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    *n_mismatch = (int64_t)bad_cells;
+    return CPM_OK;
+}
+
+int64_t cpm_kernel_launches(const cpm_handle *h) { return h ? h->launches : 0; }
+
+const char *cpm_last_error(const cpm_handle *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+void cpm_destroy(cpm_handle *h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Internal declarations of the GB300 CPM sweep library, shared by its host
+// and device translation units.  Not part of the public C ABI (include/cpm.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cpmgb {
+
+constexpr int kMaxTypes = 8;
+constexpr int kLnEntries = 129;  // LN[a], a in 0..128
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplications whose halves are mixed with the other words and a
+// round key; the key advances by the two Weyl increments after each round.
+struct Philox4 {
+    uint32_t v[4];
+};
+
+__host__ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                          uint32_t k0, uint32_t k1)
+{
+    constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
+    constexpr uint32_t kBumpA = 0x9E3779B9u, kBumpB = 0xBB67AE85u;
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+#ifdef __CUDA_ARCH__
+        const uint32_t hiA = __umulhi(kMulA, c0), loA = kMulA * c0;
+        const uint32_t hiB = __umulhi(kMulB, c2), loB = kMulB * c2;
+#else
+        const uint64_t pA = (uint64_t)kMulA * c0, pB = (uint64_t)kMulB * c2;
+        const uint32_t hiA = (uint32_t)(pA >> 32), loA = (uint32_t)pA;
+        const uint32_t hiB = (uint32_t)(pB >> 32), loB = (uint32_t)pB;
+#endif
+        const uint32_t n0 = hiB ^ c1 ^ k0;
+        const uint32_t n2 = hiA ^ c3 ^ k1;
+        c0 = n0;
+        c1 = loB;
+        c2 = n2;
+        c3 = loA;
+        k0 += kBumpA;
+        k1 += kBumpB;
+    }
+    Philox4 r;
+    r.v[0] = c0; r.v[1] = c1; r.v[2] = c2; r.v[3] = c3;
+    return r;
+}
+
+// Uniform index in [0, n) from a 32-bit draw: the high word of w*n.
+__host__ __device__ __forceinline__ uint32_t draw_below(uint32_t w, uint32_t n)
+{
+#ifdef __CUDA_ARCH__
+    return __umulhi(w, n);
+#else
+    return (uint32_t)(((uint64_t)w * n) >> 32);
+#endif
+}
+
+// Per-type model parameters, integer-scaled.
+struct TypeParams {
+    int32_t J[kMaxTypes][kMaxTypes];
+    int32_t lambda_v[kMaxTypes], v_target[kMaxTypes];
+    int32_t lambda_p[kMaxTypes], a_target[kMaxTypes];
+    int32_t lambda_act[kMaxTypes], max_act[kMaxTypes];
+    int32_t obstacle_type;
+};
+
+// Everything one round of the sweep needs.
+struct RoundArgs {
+    int32_t *lat;              // cell ids, x fastest
+    uint8_t *stamp;            // Act time stamps (MCS mod 256), or null
+    const uint8_t *cell_type;  // per cell id
+    const int32_t *Vc, *Ac;    // tallies as of the start of this round
+    int32_t *Vn, *An;          // tallies being built for the next round
+    const int4 *pend_prev;     // accepted change of the previous round, per active index
+    int4 *pend_cur;            // accepted change of this round, per active index
+    const uint32_t *thr;       // acceptance thresholds, L entries
+    const int32_t *ln_tab;     // LN[0..128]
+    const int32_t *expq;       // EXPQ[m]
+    unsigned long long *accepts;
+    int32_t L;
+    uint32_t nx, ny, nz;
+    uint32_t s, c, sd;         // block edge, divisions, sites per block
+    uint32_t nbx, nby;         // blocks per axis
+    uint32_t nax, nay;         // active blocks per axis (nbx / c, nby / c)
+    uint32_t n_active;
+    uint32_t cx, cy, cz;       // active colour, per axis
+    uint32_t t, sp, r;         // MCS (low 32 bits), sub-pass, round
+    uint32_t key0, key1;
+    TypeParams tp;
+};
+
+// Launchers (defined in the per-dimension translation units).
+cudaError_t launch_round(int dim, bool perim, bool act, const RoundArgs &a, cudaStream_t st);
+cudaError_t launch_recount(int dim, const int32_t *lat, const uint8_t *cell_type, int32_t *V, int32_t *A,
+                           uint32_t nx, uint32_t ny, uint32_t nz, cudaStream_t st);
+cudaError_t launch_compare(const int32_t *V, const int32_t *A, const int32_t *V2, const int32_t *A2, int32_t n,
+                           unsigned long long *n_bad, cudaStream_t st);
+cudaError_t launch_clamp_stamps(uint8_t *stamp, uint64_t n, uint32_t t, cudaStream_t st);
+cudaError_t launch_act_values(const int32_t *lat, const uint8_t *stamp, const uint8_t *cell_type,
+                              const TypeParams &tp, uint64_t n, uint32_t t_last, uint8_t *out, cudaStream_t st);
+
+}  // namespace cpmgb

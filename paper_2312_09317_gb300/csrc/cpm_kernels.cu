@@ -1,0 +1,333 @@
+// Device kernels of the GB300 CPM sweep: one round of copy attempts over the
+// blocks of the active checkerboard colour, plus the bookkeeping kernels
+// (tally recount and comparison, Act stamp clamp, Act read-out).
+//
+// One thread owns one active block for the round and makes its single copy
+// attempt (Results, Fig. 3A: a barrier after every attempt; here the kernel
+// boundary).  The energy change follows the paper's Methods: Eq. 1 (adhesion
+// over the Moore neighbourhood, each pair counted once; volume term), Eq. 3
+// (perimeter term) and Eq. 7/Eq. 8 (Act geometric mean), all in integers;
+// Eq. 2 acceptance through the integer threshold table.
+//
+// Tallies are double-buffered so that every attempt of a round sees the
+// tallies as they stood when the round began (deterministic form of the
+// paper's atomic updates, Fig. 2B): round g reads buffer g&1 and adds both its
+// own accepted changes and those of round g-1 into buffer (g+1)&1, which then
+// equals the state after round g.  The change of round g-1 is carried in
+// pend_prev, indexed by active-block number (equal for every colour).
+#include <cstdint>
+
+#include "cpm_internal.h"
+
+namespace cpmgb {
+namespace {
+
+constexpr int kThreads = 256;
+
+struct SmemTables {
+    int32_t J[kMaxTypes * kMaxTypes];
+    int32_t lv[kMaxTypes], vt[kMaxTypes], lp[kMaxTypes], at[kMaxTypes], la[kMaxTypes], ma[kMaxTypes];
+    int32_t ln[kLnEntries];
+};
+
+__device__ __forceinline__ void load_tables(SmemTables &sm, const RoundArgs &a, bool with_ln)
+{
+    for (int k = threadIdx.x; k < kMaxTypes * kMaxTypes; k += blockDim.x) sm.J[k] = a.tp.J[k / kMaxTypes][k % kMaxTypes];
+    if (threadIdx.x < kMaxTypes) {
+        const int k = threadIdx.x;
+        sm.lv[k] = a.tp.lambda_v[k];
+        sm.vt[k] = a.tp.v_target[k];
+        sm.lp[k] = a.tp.lambda_p[k];
+        sm.at[k] = a.tp.a_target[k];
+        sm.la[k] = a.tp.lambda_act[k];
+        sm.ma[k] = a.tp.max_act[k];
+    }
+    if (with_ln)
+        for (int k = threadIdx.x; k < kLnEntries; k += blockDim.x) sm.ln[k] = a.ln_tab[k];
+}
+
+__device__ __forceinline__ int type_of(int32_t sigma, const uint8_t *cell_type, int obstacle_type)
+{
+    return sigma < 0 ? obstacle_type : (int)__ldg(cell_type + sigma);
+}
+
+// wrapped coordinates x-1, x, x+1 along an axis of extent n
+__device__ __forceinline__ void around(uint32_t x, uint32_t n, uint32_t out[3])
+{
+    out[0] = x == 0 ? n - 1 : x - 1;
+    out[1] = x;
+    out[2] = x + 1 == n ? 0 : x + 1;
+}
+
+// Act value of a site from its stamp: Max - age, clipped at 0.
+__device__ __forceinline__ int act_value(uint8_t stamp, uint32_t t8, int max_act)
+{
+    const int age = (int)((t8 - (uint32_t)stamp) & 255u);
+    const int v = max_act - age;
+    return v > 0 ? v : 0;
+}
+
+// Integer geometric mean of Act (Q16) over site (x,y,z) with id sigma and its
+// same-cell Moore neighbours: EXPQ[(sum LN / count) >> 6]; 0 for the medium
+// or when any of those Act values is 0.
+template <int DIM>
+__device__ int64_t gm_q(const RoundArgs &a, const SmemTables &sm, uint32_t x, uint32_t y, uint32_t z, int32_t sigma,
+                        int max_act)
+{
+    if (sigma <= 0) return 0;
+    uint32_t xs[3], ys[3], zs[3];
+    around(x, a.nx, xs);
+    around(y, a.ny, ys);
+    if (DIM == 3) around(z, a.nz, zs); else zs[0] = zs[1] = zs[2] = 0;
+    int32_t sum = 0, cnt = 0;
+#pragma unroll
+    for (int dz = (DIM == 3 ? 0 : 1); dz < (DIM == 3 ? 3 : 2); ++dz) {
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+            const uint32_t row = a.nx * (ys[dy] + a.ny * zs[dz]);
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const uint32_t site = xs[dx] + row;
+                const bool centre = dx == 1 && dy == 1 && dz == 1;
+                if (!centre && a.lat[site] != sigma) continue;
+                const int v = act_value(a.stamp[site], a.t & 255u, max_act);
+                if (v == 0) return 0;
+                sum += sm.ln[v];
+                cnt += 1;
+            }
+        }
+    }
+    return (int64_t)__ldg(a.expq + ((sum / cnt) >> 6));
+}
+
+__device__ __forceinline__ int64_t floor_div_pos(int64_t num, int64_t den)
+{
+    int64_t q = num / den;
+    if (num % den != 0 && num < 0) q -= 1;
+    return q;
+}
+
+template <int DIM, bool PERIM, bool ACT>
+__global__ void __launch_bounds__(kThreads) round_kernel(const RoundArgs a)
+{
+    __shared__ SmemTables sm;
+    load_tables(sm, a, ACT);
+    __syncthreads();
+
+    constexpr int NB = DIM == 3 ? 26 : 8;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool accepted = false;
+    if (i < a.n_active) {
+        // the previous round's accepted change goes into the next tallies
+        const int4 e = a.pend_prev[i];
+        if (e.x != e.y) {
+            if (e.x > 0) { atomicAdd(a.Vn + e.x, 1); atomicAdd(a.An + e.x, e.z); }
+            if (e.y > 0) { atomicAdd(a.Vn + e.y, -1); atomicAdd(a.An + e.y, e.w); }
+        }
+
+        // the active block of this thread
+        const uint32_t ix = i % a.nax;
+        const uint32_t rest = i / a.nax;
+        const uint32_t iy = rest % a.nay;
+        const uint32_t iz = rest / a.nay;
+        const uint32_t bx = ix * a.c + a.cx, by = iy * a.c + a.cy, bz = DIM == 3 ? iz * a.c + a.cz : 0;
+        const uint32_t b = bx + a.nbx * (by + a.nby * bz);
+
+        const Philox4 w = philox4x32_10(b, a.r, a.t, a.sp, a.key0, a.key1);
+        const uint32_t jl = draw_below(w.v[0], a.sd);
+        const uint32_t jx = bx * a.s + jl % a.s;
+        const uint32_t jy = by * a.s + (jl / a.s) % a.s;
+        const uint32_t jz = DIM == 3 ? bz * a.s + jl / (a.s * a.s) : 0;
+        const uint32_t n = draw_below(w.v[1], NB);
+        const uint32_t idx = n + (n >= NB / 2 ? 1u : 0u);  // skip the centre of the 3^d stencil
+        const int ox = (int)(idx % 3), oy = (int)((idx / 3) % 3), oz = DIM == 3 ? (int)(idx / 9) : 1;
+
+        uint32_t xs[3], ys[3], zs[3];
+        around(jx, a.nx, xs);
+        around(jy, a.ny, ys);
+        if (DIM == 3) around(jz, a.nz, zs); else zs[0] = zs[1] = zs[2] = 0;
+        const uint32_t j = jx + a.nx * (jy + a.ny * jz);
+        const uint32_t isite = xs[ox] + a.nx * (ys[oy] + a.ny * zs[oz]);
+        const int32_t sj = a.lat[j];
+        const int32_t si = a.lat[isite];
+
+        int4 out = make_int4(0, 0, 0, 0);
+        if (si != sj && si >= 0 && sj >= 0) {
+            const int32_t Vj = sj > 0 ? a.Vc[sj] : 0;
+            if (!(sj > 0 && Vj <= 1)) {
+                const int ti = type_of(si, a.cell_type, a.tp.obstacle_type);
+                const int tj = type_of(sj, a.cell_type, a.tp.obstacle_type);
+                int32_t adhesion = 0;
+                int mi = 0, mj = 0;
+#pragma unroll
+                for (int dz = (DIM == 3 ? 0 : 1); dz < (DIM == 3 ? 3 : 2); ++dz) {
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy) {
+                        const uint32_t row = a.nx * (ys[dy] + a.ny * zs[dz]);
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx) {
+                            if (dx == 1 && dy == 1 && dz == 1) continue;
+                            const int32_t sn = a.lat[xs[dx] + row];
+                            const int tn = type_of(sn, a.cell_type, a.tp.obstacle_type);
+                            if (sn != si) adhesion += sm.J[ti * kMaxTypes + tn]; else ++mi;
+                            if (sn != sj) adhesion -= sm.J[tj * kMaxTypes + tn]; else ++mj;
+                        }
+                    }
+                }
+                const int dAi = NB - 2 * mi, dAj = 2 * mj - NB;
+                int64_t dh = adhesion;
+                if (si > 0) {
+                    const int64_t Vi = a.Vc[si];
+                    dh += (int64_t)sm.lv[ti] * (2 * (Vi - sm.vt[ti]) + 1);
+                    if (PERIM) {
+                        const int64_t Ai = a.Ac[si];
+                        dh += (int64_t)sm.lp[ti] * dAi * (2 * (Ai - sm.at[ti]) + dAi);
+                    }
+                }
+                if (sj > 0) {
+                    dh += (int64_t)sm.lv[tj] * (1 - 2 * ((int64_t)Vj - sm.vt[tj]));
+                    if (PERIM) {
+                        const int64_t Aj = a.Ac[sj];
+                        dh += (int64_t)sm.lp[tj] * dAj * (2 * (Aj - sm.at[tj]) + dAj);
+                    }
+                }
+                int64_t dhq = 16 * dh;
+                if (ACT) {
+                    const int tp = si > 0 ? ti : tj;
+                    const int64_t lam = sm.la[tp], mx = sm.ma[tp];
+                    if (lam != 0 && mx != 0) {
+                        const uint32_t ix_ = xs[ox], iy_ = ys[oy], iz_ = zs[oz];
+                        const int64_t gi = gm_q<DIM>(a, sm, ix_, iy_, iz_, si, si > 0 ? sm.ma[ti] : 0);
+                        const int64_t gj = gm_q<DIM>(a, sm, jx, jy, jz, sj, sj > 0 ? sm.ma[tj] : 0);
+                        dhq += floor_div_pos(lam * (gj - gi), mx * 4096);
+                    }
+                }
+                const bool ok = dhq <= 0 || (dhq < a.L && w.v[2] < __ldg(a.thr + dhq));
+                if (ok) {
+                    a.lat[j] = si;
+                    if (ACT) a.stamp[j] = (uint8_t)(si > 0 ? (a.t & 255u) : ((a.t - 128u) & 255u));
+                    if (si > 0) { atomicAdd(a.Vn + si, 1); atomicAdd(a.An + si, dAi); }
+                    if (sj > 0) { atomicAdd(a.Vn + sj, -1); atomicAdd(a.An + sj, dAj); }
+                    out = make_int4(si, sj, dAi, dAj);
+                    accepted = true;
+                }
+            }
+        }
+        a.pend_cur[i] = out;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, accepted);
+    if ((threadIdx.x & 31) == 0 && m != 0) atomicAdd(a.accepts, (unsigned long long)__popc(m));
+}
+
+template <int DIM>
+__global__ void recount_kernel(const int32_t *__restrict__ lat, int32_t *V, int32_t *A, uint32_t nx, uint32_t ny,
+                               uint32_t nz, uint64_t n)
+{
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
+        const int32_t s = lat[x];
+        if (s <= 0) continue;
+        const uint32_t px = (uint32_t)(x % nx), py = (uint32_t)((x / nx) % ny), pz = (uint32_t)(x / ((uint64_t)nx * ny));
+        uint32_t xs[3], ys[3], zs[3];
+        around(px, nx, xs);
+        around(py, ny, ys);
+        if (DIM == 3) around(pz, nz, zs); else zs[0] = zs[1] = zs[2] = 0;
+        int cnt = 0;
+        for (int dz = (DIM == 3 ? 0 : 1); dz < (DIM == 3 ? 3 : 2); ++dz)
+            for (int dy = 0; dy < 3; ++dy)
+                for (int dx = 0; dx < 3; ++dx) {
+                    if (dx == 1 && dy == 1 && dz == 1) continue;
+                    cnt += lat[xs[dx] + nx * (ys[dy] + ny * zs[dz])] != s;
+                }
+        atomicAdd(V + s, 1);
+        atomicAdd(A + s, cnt);
+    }
+}
+
+__global__ void compare_kernel(const int32_t *V, const int32_t *A, const int32_t *V2, const int32_t *A2, int32_t n,
+                               unsigned long long *n_bad)
+{
+    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        if (k > 0 && (V[k] != V2[k] || A[k] != A2[k])) atomicAdd(n_bad, 1ull);
+}
+
+// Stamps whose age is 128 or more are reset to age exactly 128, so that ages
+// stay below 256 until the next clamp (run every 64 MCS).
+__global__ void clamp_kernel(uint8_t *stamp, uint64_t n, uint32_t t)
+{
+    const uint32_t t8 = t & 255u;
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t age = (t8 - (uint32_t)stamp[x]) & 255u;
+        if (age >= 128u) stamp[x] = (uint8_t)((t8 - 128u) & 255u);
+    }
+}
+
+__global__ void act_values_kernel(const int32_t *lat, const uint8_t *stamp, const uint8_t *cell_type, TypeParams tp,
+                                  uint64_t n, uint32_t t_last, uint8_t *out)
+{
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
+        const int32_t s = lat[x];
+        int v = 0;
+        if (s > 0) v = act_value(stamp[x], t_last & 255u, tp.max_act[cell_type[s]]);
+        out[x] = (uint8_t)v;
+    }
+}
+
+unsigned grid_for(uint64_t n, unsigned threads)
+{
+    uint64_t g = (n + threads - 1) / threads;
+    if (g > 152ull * 64) g = 152ull * 64;
+    return (unsigned)(g == 0 ? 1 : g);
+}
+
+template <int DIM, bool PERIM, bool ACT>
+cudaError_t launch_round_t(const RoundArgs &a, cudaStream_t st)
+{
+    const unsigned blocks = (a.n_active + kThreads - 1) / kThreads;
+    round_kernel<DIM, PERIM, ACT><<<blocks, kThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_round(int dim, bool perim, bool act, const RoundArgs &a, cudaStream_t st)
+{
+    if (dim == 2) {
+        if (act) return perim ? launch_round_t<2, true, true>(a, st) : launch_round_t<2, false, true>(a, st);
+        return perim ? launch_round_t<2, true, false>(a, st) : launch_round_t<2, false, false>(a, st);
+    }
+    if (act) return perim ? launch_round_t<3, true, true>(a, st) : launch_round_t<3, false, true>(a, st);
+    return perim ? launch_round_t<3, true, false>(a, st) : launch_round_t<3, false, false>(a, st);
+}
+
+cudaError_t launch_recount(int dim, const int32_t *lat, const uint8_t *, int32_t *V, int32_t *A, uint32_t nx,
+                           uint32_t ny, uint32_t nz, cudaStream_t st)
+{
+    const uint64_t n = (uint64_t)nx * ny * nz;
+    if (dim == 2)
+        recount_kernel<2><<<grid_for(n, 256), 256, 0, st>>>(lat, V, A, nx, ny, nz, n);
+    else
+        recount_kernel<3><<<grid_for(n, 256), 256, 0, st>>>(lat, V, A, nx, ny, nz, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compare(const int32_t *V, const int32_t *A, const int32_t *V2, const int32_t *A2, int32_t n,
+                           unsigned long long *n_bad, cudaStream_t st)
+{
+    compare_kernel<<<grid_for((uint64_t)n, 256), 256, 0, st>>>(V, A, V2, A2, n, n_bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clamp_stamps(uint8_t *stamp, uint64_t n, uint32_t t, cudaStream_t st)
+{
+    clamp_kernel<<<grid_for(n, 256), 256, 0, st>>>(stamp, n, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_act_values(const int32_t *lat, const uint8_t *stamp, const uint8_t *cell_type, const TypeParams &tp,
+                              uint64_t n, uint32_t t_last, uint8_t *out, cudaStream_t st)
+{
+    act_values_kernel<<<grid_for(n, 256), 256, 0, st>>>(lat, stamp, cell_type, tp, n, t_last, out);
+    return cudaGetLastError();
+}
+
+}  // namespace cpmgb

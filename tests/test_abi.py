@@ -1,0 +1,107 @@
+"""The C ABI library on a machine without a GPU: it builds, loads, exports every
+function include/cpm.h declares, and rejects invalid configurations before
+touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import cpm_workloads as cw
+from paper_2312_09317_gb300 import build as B
+from paper_2312_09317_gb300 import cpm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "cpm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cpm_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return cpm.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for n in ("cpm_create", "cpm_step", "cpm_read_lattice", "cpm_stats", "cpm_destroy", "cpm_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in _declared_functions():
+        assert hasattr(lib, n), n
+        assert n in cpm._SIGNATURES, n
+
+
+def test_config_struct_layout_matches_header():
+    # offsets of the last fields follow from the C layout rules
+    assert ctypes.sizeof(cpm.Config) % 8 == 0
+    assert cpm.Config.temperature.offset % 8 == 0
+    assert cpm.Config.seed.offset % 8 == 0
+
+
+def _create(w, **over):
+    keep = []
+    cfg = cpm.make_config(w, keep)
+    for k, v in over.items():
+        setattr(cfg, k, v)
+    h = ctypes.c_void_p()
+    rc = cpm.load().cpm_create(ctypes.byref(cfg), None, ctypes.byref(h))
+    return rc, cpm.load().cpm_last_error(None).decode()
+
+
+@pytest.mark.parametrize("field,value,msg", [
+    ("dim", 4, "dim"),
+    ("a", 6, "multiples of a"),
+    ("c", 1, "c >= 2"),
+    ("a", 2, "c >= 2"),
+    ("P", 3, "P must divide"),
+    ("temperature", 0.0, "temperature"),
+    ("temperature", 1e6, "temperature"),
+    ("obstacle_type", 0, "obstacle_type"),
+    ("n_cells", -1, "n_cells"),
+    ("t0", -5, "t0"),
+])
+def test_invalid_configs_are_rejected_without_a_gpu(lib, field, value, msg):
+    w = cw.random_small(1, dim=2, n=16, n_cells=3, a=4, c=2, P=1)
+    rc, err = _create(w, **{field: value})
+    assert rc == cpm.CPM_E_INVALID
+    assert msg in err
+
+
+def test_gap_between_active_blocks_is_enforced(lib):
+    # a = 4, c = 4 gives blocks of edge 1 that are 3 apart: fine; a = 3, c = 3 would be 2 apart: fine;
+    # a = 2, c = 2 gives blocks 1 apart: rejected
+    w = cw.random_small(1, dim=2, n=16, n_cells=3, a=2, c=2, P=1)
+    rc, err = _create(w)
+    assert rc == cpm.CPM_E_INVALID and "apart" in err
+
+
+def test_bad_lattice_and_act_rejected(lib):
+    w = cw.random_small(2, dim=2, n=16, n_cells=3, a=4, act=True)
+    lat = w.lattice.copy()
+    lat.flat[5] = 99
+    rc, err = _create(w.replace(lattice=lat))
+    assert rc == cpm.CPM_E_INVALID and "init_lattice" in err
+    act = w.act.copy()
+    act[w.lattice == 0] = 0
+    act.flat[np.flatnonzero(w.lattice.ravel() == 0)[0]] = 3
+    rc, err = _create(w.replace(act=act))
+    assert rc == cpm.CPM_E_INVALID and "init_act" in err
+    J = w.J.copy()
+    J[1, 2] += 1
+    rc, err = _create(w.replace(J=J))
+    assert rc == cpm.CPM_E_INVALID and "symmetric" in err
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.cpm_step(None, 1) == cpm.CPM_E_HANDLE
+    assert lib.cpm_read_lattice(None, None, 0) == cpm.CPM_E_HANDLE
+    assert lib.cpm_kernel_launches(None) == 0
+    lib.cpm_destroy(None)
