@@ -1,0 +1,337 @@
+"""Benchmark of the parallel CPM copy-attempt sweep on GB300.
+
+A step is one Monte Carlo step (MCS): one copy attempt per lattice site,
+issued as P cycles x c^d colour sub-passes x k rounds of the checkerboard
+scheme, all in the CUDA library's kernels.  The metric is copy attempts per
+second (every attempt counts, early rejects included) and the fraction of
+the HBM roofline of the round kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   # the CPU oracle, timed on host cores
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (the scheme needs no data exchange between replicas); the value is
+the attempts of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import cpm_workloads as cw  # noqa: E402
+
+METRIC = "copy attempts/s"
+UNIT = "attempts/s"
+
+# Workloads: (factory, algorithmic bytes per site per MCS, description)
+# bytes: int32 lattice read + write (8 B); with Act the uint8 stamp read + write (2 B).
+WORKLOADS = {
+    "cpm3d_256": (lambda: cw.config2_3d(seed=1, n=256, a=4, c=2, P=8), 8,
+                  "3D 256^3 Moore-26, ~17,576 cells, V_t=500, A_t=400, lambda_V=25, lambda_P=0.5, "
+                  "J(c,c)=20, J(c,m)=12, T=20 (x2 integer scale); a=4, c=2, P=8"),
+    # the same model on a lattice larger than L2, for DRAM counters
+    "cpm3d_512": (lambda: cw.config2_3d(seed=1, n=512, a=4, c=2, P=8), 8,
+                  "3D 512^3, otherwise as cpm3d_256"),
+}
+DEFAULT_WORKLOAD = "cpm3d_256"
+
+# DRAM bytes per round-kernel launch from the last ncu capture, valid only for
+# the kernel source it was taken on (sha1 of csrc/cpm_kernels.cu, first 12 hex).
+NCU_TRAFFIC = {}
+
+
+def kernel_hash() -> str:
+    p = os.path.join(ROOT, "paper_2312_09317_gb300", "csrc", "cpm_kernels.cu")
+    return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("CPM_BENCH_BACKEND") != "gloo" else "gloo")
+        return ws, rank, local, dist
+    return 1, 0, 0, None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x: float) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, x: float) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (the --impl reference arm and the cpu_baseline object)
+# ----------------------------------------------------------------------------
+
+def oracle_sample(w, budget_s: float):
+    """Time oracle (a), the serial CPM, single-threaded on this host over whole
+    MCS of the workload until about budget_s seconds; returns attempts/s."""
+    import oracle
+    st = oracle.State(w)
+    n_mcs, t_used = 0, 0.0
+    while t_used < budget_s:
+        t0 = time.perf_counter()
+        st.serial_run(1)
+        t_used += time.perf_counter() - t0
+        n_mcs += 1
+    return n_mcs * w.n_sites / t_used, n_mcs, t_used
+
+
+def run_reference(args):
+    ws, rank, local, dist = dist_init()
+    if rank != 0:
+        return 0
+    w = WORKLOADS[args.workload][0]()
+    import oracle
+    st = oracle.State(w)
+    for _ in range(args.warmup):
+        st.serial_run(1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        st.serial_run(1)
+        times.append(time.perf_counter() - t0)
+    T = sum(times)
+    value = args.steps * w.n_sites / T
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": {"workload": args.workload, "sites": w.n_sites, "cells": w.n_cells},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "serial CPM oracle (a), one thread, %d whole MCS after %d warm-up MCS of "
+                                   "the full workload" % (args.steps, args.warmup)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    from paper_2312_09317_gb300 import build as B
+    from paper_2312_09317_gb300 import cpm
+
+    ws, rank, local, dist = dist_init()
+    torch.cuda.set_device(local)
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    barrier(dist)
+    factory, bytes_per_site, desc = WORKLOADS[args.workload]
+    w = factory()
+    w = w.replace(seed=w.seed + 1000 * rank)  # independent replicas
+    stream = torch.cuda.Stream()
+    sim = cpm.Sim(w, stream=stream)
+    n = w.n_sites
+    per_mcs = w.P * w.c ** w.dim
+    rounds = per_mcs * (((w.a // w.c) ** w.dim) // w.P)
+    lattice_bytes = 4 * n
+    flush_l2 = lattice_bytes * 2 < 256 * 2 ** 20
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.int32, device="cuda") if flush_l2 else None
+
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    l0 = sim.launches()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(dist)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                flush.fill_(k)
+        with torch.cuda.stream(stream):
+            ev[k][0].record(stream)
+            sim.step(1)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    clk = clocks.stop()
+    launches = sim.launches() - l0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = sum(step_ms) / 1e3
+    t_max = max_over_ranks(dist, t_local)
+    attempts_all = sum_over_ranks(dist, float(args.steps * n))
+    value = attempts_all / t_max
+
+    # per-launch duration of the round kernel: sub-passes (k = 1: one round each) timed alone
+    sub = []
+    with torch.cuda.stream(stream):
+        for k in range(min(64, per_mcs * 4)):
+            if flush is not None:
+                flush.fill_(k)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim.step_subpasses(1)
+            b.record(stream)
+            sub.append((a, b))
+    torch.cuda.synchronize()
+    k_rounds = ((w.a // w.c) ** w.dim) // w.P
+    launch_ms = statistics.mean(a.elapsed_time(b) for a, b in sub) / k_rounds
+    peak, peak_kind = peaks()
+    alg_bytes_launch = bytes_per_site * n / rounds
+    achieved = alg_bytes_launch / (launch_ms / 1e3) / 1e9
+    khash = kernel_hash()
+    traffic = NCU_TRAFFIC.get((args.workload, khash))
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    host = torch.empty((w.nz, w.ny, w.nx), dtype=torch.int32, pin_memory=True).numpy()
+    sim.read_lattice(host)
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.load_lattice(host)      # H2D of the step's input + tally recount
+        sim.step(1)
+        sim.read_lattice(host)      # D2H of the step's result (synchronises)
+    e2e_local = time.perf_counter() - t0
+    e2e_t = max_over_ranks(dist, e2e_local)
+    e2e_value = sum_over_ranks(dist, float(e2e_steps * n)) / e2e_t
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, n_mcs, t_used = oracle_sample(w, args.cpu_budget)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "serial CPM oracle (a), one thread, the first %d MCS of the same workload from its "
+                         "initial state (%.1f s)" % (n_mcs, t_used)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "sites": n, "cells": w.n_cells,
+                       "rounds_per_mcs": rounds, "l2": "flushed between timed steps (512 MiB write)"
+                       if flush_l2 else "inputs larger than L2", "parallelism": "replicas" if ws > 1 else "1 GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": "of %s" % peak_kind,
+                         "kernel": "round_kernel", "launch_ms": launch_ms,
+                         "alg_bytes_per_launch": alg_bytes_launch},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": lattice_bytes,
+                    "d2h_bytes_per_step": lattice_bytes, "steps": e2e_steps},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
