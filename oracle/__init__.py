@@ -9,7 +9,7 @@ The arithmetic lives in ``cpm_oracle.c`` (plain C, compiled with gcc by
 ``build()``); this module marshals numpy arrays into it with ctypes.
 
 * ``serial_run``  -- oracle (a): the serial CPM chain (Methods, Eq. 1, Eq. 2,
-  Eq. 3, Eq. 7, Eq. 8) in double precision with exact exp.
+  Eq. 3, Eq. 8, Eq. 9) in double precision with exact exp.
 * ``replay_run``  -- oracle (b): replay of the parallel checkerboard scheme
   (Results, Fig. 2A/B, Fig. 3A/B) with Philox counters, integer energies and
   the integer threshold table.

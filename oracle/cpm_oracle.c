@@ -220,7 +220,7 @@ static int64_t delta_h_int(const orc_params *p, const int32_t *lat, int64_t j, i
 }
 
 /* ------------------------------------------------------------------ */
-/* Act model (Eq. 7 and Eq. 8).  GM(x) is the geometric mean of Act     */
+/* Act model (Eq. 8 and Eq. 9).  GM(x) is the geometric mean of Act     */
 /* over x and those of its Moore neighbours that belong to the same     */
 /* cell; it is 0 for medium sites and whenever one of those Act values  */
 /* is 0.  The energy change is (lambda_act/Max_act)(GM(j) - GM(i)), the */

@@ -6,7 +6,7 @@
 // attempt (Results, Fig. 3A: a barrier after every attempt; here the kernel
 // boundary).  The energy change follows the paper's Methods: Eq. 1 (adhesion
 // over the Moore neighbourhood, each pair counted once; volume term), Eq. 3
-// (perimeter term) and Eq. 7/Eq. 8 (Act geometric mean), all in integers;
+// (perimeter term) and Eq. 8/Eq. 9 (Act term, geometric mean), all in integers;
 // Eq. 2 acceptance through the integer threshold table.
 //
 // Tallies are double-buffered so that every attempt of a round sees the
