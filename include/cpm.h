@@ -10,7 +10,7 @@
  *                   each unordered pair counted once; volume term) and Eq. 3
  *                   (perimeter term, A = interfaces with other ids);
  *   acceptance      Methods, Eq. 2: min(1, exp(-dH/T));
- *   Act motility    Methods, Eq. 7 and Eq. 8 (geometric mean of Act over the
+ *   Act motility    Methods, Eq. 8 and Eq. 9 (geometric mean of Act over the
  *                   site and its same-cell Moore neighbours; Act set to
  *                   Max_act on update, decays by 1 per MCS);
  *   parallel scheme Results, "Designing a parallel execution scheme" and
@@ -77,7 +77,8 @@ enum {
     CPM_E_NOMEM = -2,     /* device or host allocation failed */
     CPM_E_CUDA = -3,      /* a CUDA runtime call failed */
     CPM_E_HANDLE = -4,    /* NULL or destroyed handle */
-    CPM_E_STATE = -5      /* device-side consistency check failed */
+    CPM_E_STATE = -5,     /* device-side consistency check failed */
+    CPM_E_LIMIT = -6      /* a size exceeds the fixed scratch of cpm_step_noalloc */
 };
 
 typedef struct cpm_config {
@@ -161,6 +162,45 @@ const char *cpm_last_error(const cpm_handle *h);
 
 /* Free every resource of h (NULL is ignored).  Synchronises the stream. */
 void cpm_destroy(cpm_handle *h);
+
+/* cpm_step_noalloc -- the sweep without any device allocation.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc, e.g. a host framework or plug-in that owns the
+ * GPU's memory budget and only hands out fixed buffers, or code that must not
+ * allocate while it runs because an allocation could block, fail half way or
+ * escape the caller's memory accounting.  It runs n_subpasses sub-passes of
+ * the same round kernel as cpm_step, from position (t, sp) (MCS index and
+ * sub-pass within it), directly on the caller's device buffers:
+ *   lattice    device, nx*ny*nz int32, read and updated in place;
+ *   V, A       device, n_cells + 1 int32 each: the exact volume and interface
+ *              tallies of that lattice on entry (e.g. from cpm_read_tallies),
+ *              updated in place;
+ *   cell_type  device, n_cells + 1 uint8.
+ * cfg gives the model and schedule (its host pointer fields are ignored; the
+ * lattice contents are not validated).  The result equals what a handle at
+ * the same position would produce with cpm_step_subpasses.
+ *
+ * It allocates nothing: all scratch (second tally buffer, pending-change
+ * buffers, threshold/log/exp tables, accept counter) lives in one fixed
+ * file-scope device array of about 8.8 MiB, present on every GPU that loads
+ * the library until the process exits.  Limits, beyond which the call
+ * returns CPM_E_LIMIT without doing anything: at most 262,144 active blocks
+ * per round (nx*ny*nz / a^d), at most 65,535 cells, a threshold table of at
+ * most 32,768 entries (temperature up to about 92 in scaled units), and no
+ * Act term.
+ * The first call on a device looks up the array's device address with that
+ * device current (a one-time set-up); make that first call before any stream
+ * capture.  Every call shares the array and finds the previous call's
+ * contents there; the call re-initialises everything it reads, but calls
+ * that overlap on the GPU (other streams, other threads) race on it and must
+ * be serialised by the caller.  Work is queued on cuda_stream; when accepts
+ * is not NULL the call waits for it and stores the number of accepted copies
+ * of this call there.  Returns CPM_OK, CPM_E_LIMIT, CPM_E_INVALID or
+ * CPM_E_CUDA (cpm_last_error does not report on this call). */
+int cpm_step_noalloc(const cpm_config *cfg, int32_t *lattice, int32_t *V, int32_t *A,
+                     const uint8_t *cell_type, int64_t t, int32_t sp, int64_t n_subpasses,
+                     void *cuda_stream, int64_t *accepts);
 
 #ifdef __cplusplus
 }

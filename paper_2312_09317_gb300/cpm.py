@@ -17,7 +17,7 @@ from . import build as _build
 
 MAX_TYPES = 8
 
-CPM_OK, CPM_E_INVALID, CPM_E_NOMEM, CPM_E_CUDA, CPM_E_HANDLE, CPM_E_STATE = 0, -1, -2, -3, -4, -5
+CPM_OK, CPM_E_INVALID, CPM_E_NOMEM, CPM_E_CUDA, CPM_E_HANDLE, CPM_E_STATE, CPM_E_LIMIT = 0, -1, -2, -3, -4, -5, -6
 
 
 class Config(ctypes.Structure):
@@ -65,6 +65,9 @@ _SIGNATURES = {
     "cpm_kernel_launches": (ctypes.c_int64, [ctypes.c_void_p]),
     "cpm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "cpm_destroy": (None, [ctypes.c_void_p]),
+    "cpm_step_noalloc": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
+                                        ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
 }
 
 _lib = None
