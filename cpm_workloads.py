@@ -109,19 +109,34 @@ def jittered_centres(shape, spacing: float, jitter: float, rng) -> np.ndarray:
 
 def place_cubes(lattice: np.ndarray, centres: np.ndarray, edge: int) -> int:
     """Write cubes (squares in 2D) of the given edge, periodic, with ids
-    1..len(centres) in centre order.  Sites that are not medium (obstacle or
-    an earlier cube) are left alone.  Returns the number of cells placed."""
+    1..len(centres) in centre order.  A site claimed by several cubes goes to
+    the lowest id; sites that are not medium (obstacles) are left alone.
+    Returns the number of cells (len(centres))."""
     dim = lattice.ndim
+    shape = np.array(lattice.shape, dtype=np.int64)
     lo = -(edge // 2)
     offs = np.stack(np.meshgrid(*([np.arange(lo, lo + edge)] * dim), indexing="ij"),
                     axis=-1).reshape(-1, dim)
-    n = 0
-    for cid, ctr in enumerate(centres, start=1):
-        pts = (ctr[None, :] + offs) % np.array(lattice.shape)[None, :]
-        idx = tuple(pts[:, d] for d in range(dim))
-        free = lattice[idx] == 0
-        lattice[tuple(p[free] for p in idx)] = cid
-        n = cid
+    n = len(centres)
+    if n == 0:
+        return 0
+    flat = np.zeros(n * len(offs), dtype=np.int64)
+    stride = 1
+    for d in reversed(range(dim)):
+        coord = (centres[:, None, d].astype(np.int64) + offs[None, :, d]) % shape[d]
+        flat += coord.reshape(-1) * stride
+        stride *= shape[d]
+    ids = np.repeat(np.arange(1, n + 1, dtype=np.int32), len(offs))
+    # first claim (lowest id) per site
+    order = np.argsort(flat, kind="stable")
+    fs = flat[order]
+    first = np.ones(len(fs), dtype=bool)
+    first[1:] = fs[1:] != fs[:-1]
+    sites = fs[first]
+    owner = ids[order][first]
+    lv = lattice.reshape(-1)
+    free = lv[sites] == 0
+    lv[sites[free]] = owner[free]
     return n
 
 
@@ -187,42 +202,48 @@ def fibre_mask(shape, rng, cell_spacing: float = 48.0, frac: float = 0.15,
     Voronoi seeds sit on a jittered grid of the given spacing; a voxel lies on
     the network when its nearest and third-nearest seeds are almost equally
     far (it is close to a line where three Voronoi regions meet).  The
-    closeness threshold is chosen as the ``frac`` quantile of that gap, so the
-    mask freezes ``frac`` of the voxels.  Periodic.  Uses torch (on ``device``
-    if given) only to evaluate distances quickly."""
+    closeness threshold is the ``frac`` quantile of that gap, so the mask
+    freezes ``frac`` of the voxels.  Periodic.  Uses torch (on ``device`` if
+    given) only to evaluate distances quickly."""
     import torch
     dev = torch.device(device or "cpu")
-    shape = tuple(int(s) for s in shape)
-    g = [max(1, int(round(n / cell_spacing))) for n in shape]
+    shape = tuple(int(x) for x in shape)
+    g = [max(4, int(round(n / cell_spacing))) for n in shape]
     step = [shape[d] / g[d] for d in range(3)]
     jit = rng.uniform(-0.4, 0.4, size=(g[0], g[1], g[2], 3))
     base = np.stack(np.meshgrid(*[np.arange(m) for m in g], indexing="ij"), axis=-1)
     seeds = (base + 0.5 + jit) * np.array(step)[None, None, None, :]
     seeds_t = torch.tensor(seeds, dtype=torch.float32, device=dev)
-    gz, gy, gx = g
     nz, ny, nx = shape
-    out = np.zeros(shape, dtype=np.float32)
     # candidate seeds: the 4x4x4 grid cells around each voxel's own cell
     offs = torch.tensor([(i, j, k) for i in range(-2, 2) for j in range(-2, 2) for k in range(-2, 2)],
                         device=dev)
     L = torch.tensor([nz, ny, nx], dtype=torch.float32, device=dev)
+    gt = torch.tensor(g, device=dev)
+    st = torch.tensor(step, dtype=torch.float32, device=dev)
     yy, xx = torch.meshgrid(torch.arange(ny, device=dev), torch.arange(nx, device=dev), indexing="ij")
-    for z in range(nz):
-        p = torch.stack([torch.full_like(yy, z), yy, xx], dim=-1).float() + 0.5   # [ny, nx, 3]
-        cell = torch.stack([(p[..., d] / step[d]).floor().long() for d in range(3)], dim=-1)
-        frac_in = torch.stack([p[..., d] / step[d] - cell[..., d] for d in range(3)], dim=-1)
-        # choose the 4 cells along each axis so the voxel sits in the middle two
-        shift = (frac_in >= 0.5).long()
-        cand = cell[..., None, :] + offs[None, None, :, :] + shift[..., None, :]
-        ci = torch.stack([cand[..., d] % g[d] for d in range(3)], dim=-1)
-        sp = seeds_t[ci[..., 0], ci[..., 1], ci[..., 2]]      # [ny, nx, 64, 3]
+    gap = torch.empty(shape, dtype=torch.float16, device=dev)
+    zc = max(1, min(nz, (1 << 22) // (ny * nx)))
+    for z0 in range(0, nz, zc):
+        z1 = min(nz, z0 + zc)
+        zz = torch.arange(z0, z1, device=dev)[:, None, None].expand(z1 - z0, ny, nx)
+        p = torch.stack([zz, yy.expand_as(zz), xx.expand_as(zz)], dim=-1).float() + 0.5
+        q = p / st
+        cell = q.floor().long()
+        shift = ((q - cell) >= 0.5).long()
+        cand = cell[..., None, :] + offs + shift[..., None, :]
+        ci = cand % gt
+        sp = seeds_t[ci[..., 0], ci[..., 1], ci[..., 2]]
         d = sp - p[..., None, :]
         d = d - torch.round(d / L) * L
         dist = d.norm(dim=-1)
         top = torch.topk(dist, 3, dim=-1, largest=False).values
-        out[z] = (top[..., 2] - top[..., 0]).cpu().numpy()
-    thr = np.quantile(out[:: max(1, nz // 64)], frac)
-    return out < thr
+        gap[z0:z1] = (top[..., 2] - top[..., 0]).half()
+    flat = gap.reshape(-1)
+    gen = torch.Generator(device="cpu").manual_seed(int(rng.integers(1 << 31)))
+    idx = torch.randint(0, flat.numel(), (min(flat.numel(), 1 << 22),), generator=gen).to(dev)
+    thr = torch.quantile(flat[idx].float(), frac)
+    return (gap < thr.half()).cpu().numpy()
 
 
 def config3_3d(seed: int = 1, n: int = 1024, a: int = 8, c: int = 2, P: int = 2,
@@ -235,7 +256,8 @@ def config3_3d(seed: int = 1, n: int = 1024, a: int = 8, c: int = 2, P: int = 2,
     lambda_V=25, lambda_P=0.2, T=20, all scaled by S=5."""
     rng = np.random.default_rng(seed)
     shape = (n, n, n)
-    fib = fibre_mask(shape, rng, cell_spacing=min(fibre_spacing, n / 2), device=device)
+    # at least 4 Voronoi seeds per axis, so the 4x4x4 candidate window never wraps onto itself
+    fib = fibre_mask(shape, rng, cell_spacing=min(fibre_spacing, n / 4), device=device)
     lat = np.zeros(shape, dtype=np.int32)
     lat[fib] = -1
     ctr = jittered_centres(shape, 10.0, 2.0, rng)

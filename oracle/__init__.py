@@ -104,7 +104,7 @@ class State:
     """Oracle state for one workload: lattice, Act values, tallies, position.
     Keeps a reference to every array handed to C."""
 
-    def __init__(self, w, act_on=None):
+    def __init__(self, w, act_on=None, recount=True):
         self.w = w
         self.lattice = np.ascontiguousarray(w.lattice, dtype=np.int32).copy()
         self.cell_type = np.ascontiguousarray(w.cell_type, dtype=np.uint8).copy()
@@ -117,8 +117,9 @@ class State:
         self.params = make_params(w, self.cell_type)
         self.V = np.zeros(w.n_cells + 1, dtype=np.int32)
         self.A = np.zeros(w.n_cells + 1, dtype=np.int32)
-        lib().orc_recount(ctypes.byref(self.params), _ptr(self.lattice, ctypes.c_int32),
-                          _ptr(self.V, ctypes.c_int32), _ptr(self.A, ctypes.c_int32))
+        if recount:
+            lib().orc_recount(ctypes.byref(self.params), _ptr(self.lattice, ctypes.c_int32),
+                              _ptr(self.V, ctypes.c_int32), _ptr(self.A, ctypes.c_int32))
         self.t = 0
         self.sp = 0
         self.rng = (ctypes.c_uint64 * 4)()

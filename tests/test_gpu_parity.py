@@ -186,3 +186,67 @@ def test_load_lattice_resets_tallies(cpm):
     out = torch.empty_like(d)
     sim.read_lattice(out)
     assert torch.equal(out, d)
+
+
+def test_config3_tissue_small_bit_exact(cpm):
+    """The tissue workload (fibre obstacles, Act, perimeter, 26-neighbourhood)
+    at 64^3, bit-exact after every MCS."""
+    w = cw.config3_3d(seed=2, n=64, a=4, c=2, P=8, device="cuda")
+    assert (w.lattice < 0).mean() > 0.1
+    sim = cpm.Sim(w)
+    ref = oracle.State(w)
+    for m in range(3):
+        sim.step(1)
+        ref.replay_run(1)
+        _compare(sim, ref, "tissue 64^3 after MCS %d" % m)
+    assert sim.verify() == 0
+
+
+def test_config3_full_size_sampled(cpm):
+    """1024^3 tissue workload in the launch configuration bench.py times
+    (a=4, c=2, P=8: one round per sub-pass).  After 2 MCS and 3 sub-passes,
+    one more round runs on the GPU; the oracle replays that round for 4,096
+    sampled active blocks from the GPU's state before it, and their sites and
+    Act values must match.  Tallies are checked at full size by a device
+    recount, obstacles by comparison with the input."""
+    w = cw.config3_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda")
+    sim = cpm.Sim(w)
+    sim.step(2)
+    sim.step_subpasses(3)
+    st = sim.stats()
+    t, sp = st["mcs"], st["subpass"]
+    assert sp == 3
+    pre_lat = sim.read_lattice()
+    pre_act = sim.read_act()
+    V, A = sim.read_tallies()
+    sim.step_subpasses(1)
+    post_lat = sim.read_lattice()
+    post_act = sim.read_act()
+    assert sim.verify() == 0
+    assert np.array_equal(post_lat < 0, w.lattice < 0)
+
+    ref = oracle.State(w.replace(lattice=pre_lat, act=pre_act), recount=False)
+    ref.V[:] = V
+    ref.A[:] = A
+    s = w.a // w.c
+    C = w.c ** 3
+    col = oracle.colour_perm(w, t, sp // C)[sp % C]
+    cx, cy, cz = col % w.c, (col // w.c) % w.c, col // (w.c * w.c)
+    nb = w.nx // s
+    rng = np.random.default_rng(7)
+    k = 4096
+    bx = rng.integers(0, nb // w.c, k) * w.c + cx
+    by = rng.integers(0, nb // w.c, k) * w.c + cy
+    bz = rng.integers(0, nb // w.c, k) * w.c + cz
+    blocks = np.unique(bx + nb * (by + nb * bz))
+    ref.replay_blocks(t, sp, 0, blocks)
+    bxs, bys, bzs = blocks % nb, (blocks // nb) % nb, blocks // (nb * nb)
+    for dz in range(s):
+        for dy in range(s):
+            for dx in range(s):
+                z, y, x = bzs * s + dz, bys * s + dy, bxs * s + dx
+                assert np.array_equal(post_lat[z, y, x], ref.lattice[z, y, x])
+                assert np.array_equal(post_act[z, y, x], ref.act[z, y, x])
+    changed = int((pre_lat != post_lat).sum())
+    assert changed > 0
+    sim.close()
