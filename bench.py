@@ -49,6 +49,16 @@ WORKLOADS = {
                           "J(c,fibre)=40, lambda_V=25, lambda_P=0.2, T=20 (x5 integer scale); a=4, c=2, P=8"),
     "cpm3d_tissue_512": (lambda: cw.config3_3d(seed=1, n=512, a=4, c=2, P=8, device="cuda"), 10,
                          "3D tissue 512^3, otherwise as cpm3d_tissue_1024"),
+    # the tissue workload under the tiled schedule (tiles of edge 16, one tile cycle per MCS)
+    "cpm3d_tissue_1024_tiled": (lambda: cw.config3_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda")
+                                .replace(tile=16, tile_cycles=1), 10,
+                                "as cpm3d_tissue_1024, tiled schedule: tiles of edge 16, 1 tile cycle per MCS"),
+    "cpm3d_tissue_1024_tiled2": (lambda: cw.config3_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda")
+                                 .replace(tile=16, tile_cycles=2), 10,
+                                 "as cpm3d_tissue_1024, tiled schedule: tiles of edge 16, 2 tile cycles per MCS"),
+    "cpm3d_tissue_512_tiled": (lambda: cw.config3_3d(seed=1, n=512, a=4, c=2, P=8, device="cuda")
+                               .replace(tile=16, tile_cycles=1), 10,
+                               "3D tissue 512^3, tiled schedule: tiles of edge 16"),
 }
 DEFAULT_WORKLOAD = "cpm3d_tissue_1024"
 
@@ -242,6 +252,9 @@ def run_gpu(args):
     n = w.n_sites
     per_mcs = w.P * w.c ** w.dim
     rounds = per_mcs * (((w.a // w.c) ** w.dim) // w.P)
+    if w.tile:
+        per_mcs = w.tile_cycles * 2 ** w.dim   # epochs per MCS
+        rounds = per_mcs                       # one launch per epoch
     lattice_bytes = 4 * n
     flush_l2 = lattice_bytes * 2 < 256 * 2 ** 20
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.int32, device="cuda") if flush_l2 else None
@@ -286,7 +299,7 @@ def run_gpu(args):
             b.record(stream)
             sub.append((a, b))
     torch.cuda.synchronize()
-    k_rounds = ((w.a // w.c) ** w.dim) // w.P
+    k_rounds = 1 if w.tile else ((w.a // w.c) ** w.dim) // w.P
     launch_ms = statistics.mean(a.elapsed_time(b) for a, b in sub) / k_rounds
     peak, peak_kind = peaks()
     alg_bytes_launch = bytes_per_site * n / rounds
@@ -328,7 +341,7 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": "of %s" % peak_kind,
-                         "kernel": "round_kernel", "launch_ms": launch_ms,
+                         "kernel": "tile_epoch_kernel" if w.tile else "round_kernel", "launch_ms": launch_ms,
                          "alg_bytes_per_launch": alg_bytes_launch},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": lattice_bytes,

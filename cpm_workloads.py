@@ -60,6 +60,8 @@ class Workload:
     cell_type: np.ndarray    # uint8 [n_cells + 1]; entry 0 is the medium
     act: Optional[np.ndarray] = None  # uint8 [nz, ny, nx] initial Act values
     n_mcs: int = 1
+    tile: int = 0            # tiled schedule: tile edge T (0: global rounds)
+    tile_cycles: int = 1     # tiled schedule: tile cycles per MCS
 
     @property
     def n_cells(self) -> int:

@@ -39,6 +39,19 @@
  *     point through integer tables; acceptance compares the uint32 draw with
  *     THR[dH] = min(2^32-1, floor(2^32 exp(-dH/(16T)))).
  *   - A copy that would remove a cell's last site is rejected.
+ *   - Tiled schedule (tile = T > 0): the same sub-passes, rounds and Philox
+ *     counters, executed tile by tile.  Tiles of edge T (a multiple of a;
+ *     every extent a multiple of 2T) sit on a grid shifted per MCS by a
+ *     Philox offset (counter (0, 0, MCS, 2<<24), words 0..2 -> a multiple
+ *     of a below T per axis); a tile's colour is the parity of its tile
+ *     coordinates.  Per MCS, P_T tile cycles visit the 2^d tile colours in
+ *     a Philox order (swap i from counter (i, cycle, MCS, 3<<24)); in such
+ *     an epoch every tile of the colour runs, on its own blocks, the
+ *     epoch's P*c^d/P_T sub-passes with all their rounds, while the tiles
+ *     around it are dormant.  Tallies read by a tile are those at the start
+ *     of the epoch plus the tile's own changes of earlier rounds.  A tile
+ *     and its 2-site halo may hold at most 510 distinct cells; beyond that
+ *     the epoch is invalid and the next reading call returns CPM_E_STATE.
  *   The result is a deterministic function of (config, seed, number of
  *   sub-passes run): cpm_step(h, a) then cpm_step(h, b) equals
  *   cpm_step(h, a + b), on any GPU.
@@ -100,11 +113,13 @@ typedef struct cpm_config {
     const int32_t *init_lattice; /* host, nx*ny*nz ids in -1..n_cells */
     const uint8_t *init_act;     /* host, nx*ny*nz Act values or NULL (all 0) */
     int64_t t0;                  /* MCS index of the first MCS to run (>= 0) */
+    int32_t tile;                /* 0: global rounds; T > 0: tiled schedule with tiles of edge T */
+    int32_t tile_cycles;         /* tiled schedule: tile cycles per MCS (P_T, divides P) */
 } cpm_config;
 
 typedef struct cpm_stats_t {
-    int64_t mcs;            /* MCS index of the next sub-pass (completed MCS if sp == 0) */
-    int32_t subpass;        /* next sub-pass within that MCS */
+    int64_t mcs;            /* MCS index of the next unit (completed MCS if subpass == 0) */
+    int32_t subpass;        /* next schedule unit (sub-pass or epoch) within that MCS */
     int32_t n_live_cells;   /* cells with V > 0 */
     int64_t attempts;       /* copy attempts made by this handle */
     int64_t accepts;        /* accepted copies made by this handle */
@@ -124,8 +139,9 @@ int cpm_create(const cpm_config *cfg, void *cuda_stream, cpm_handle **out);
  * the handle's stream.  n_mcs >= 0. */
 int cpm_step(cpm_handle *h, int64_t n_mcs);
 
-/* Run n sub-passes (colour visits); cpm_step(h, m) = cpm_step_subpasses(h,
- * m * P * c^d).  Used for finer-grained checks.  n >= 0. */
+/* Run n schedule units: sub-passes (colour visits) of the global schedule,
+ * epochs of the tiled one; cpm_step(h, m) = cpm_step_subpasses(h, m * P * c^d)
+ * (global) or (h, m * P_T * 2^d) (tiled).  Used for finer-grained checks. */
 int cpm_step_subpasses(cpm_handle *h, int64_t n);
 
 /* Copy the lattice (nx*ny*nz int32) to dst (host if dst_is_device == 0,
@@ -178,7 +194,7 @@ void cpm_destroy(cpm_handle *h);
  *              updated in place;
  *   cell_type  device, n_cells + 1 uint8.
  * cfg gives the model and schedule (its host pointer fields are ignored; the
- * lattice contents are not validated).  The result equals what a handle at
+ * lattice contents are not validated; only the global schedule, tile = 0).  The result equals what a handle at
  * the same position would produce with cpm_step_subpasses.
  *
  * It allocates nothing: all scratch (second tally buffer, pending-change

@@ -57,6 +57,8 @@ class Params(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("n_cells", ctypes.c_int32),
         ("cell_type", ctypes.POINTER(ctypes.c_uint8)),
+        ("tile", ctypes.c_int32),
+        ("tile_cycles", ctypes.c_int32),
     ]
 
 
@@ -153,6 +155,9 @@ class State:
         return acc.value
 
     def subpasses_per_mcs(self) -> int:
+        """Schedule units per MCS: sub-passes (global rounds) or epochs (tiled)."""
+        if getattr(self.w, "tile", 0):
+            return self.w.tile_cycles * 2 ** self.w.dim
         return self.w.P * self.w.c ** self.w.dim
 
     def replay_run(self, n_mcs: int) -> int:
@@ -209,6 +214,8 @@ def make_params(w, cell_type: np.ndarray) -> Params:
     p.seed = w.seed
     p.n_cells = w.n_cells
     p.cell_type = cell_type.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    p.tile = int(getattr(w, "tile", 0))
+    p.tile_cycles = int(getattr(w, "tile_cycles", 1))
     return p
 
 

@@ -56,6 +56,8 @@ typedef struct {
     uint64_t seed;
     int32_t n_cells;
     const uint8_t *cell_type; /* n_cells + 1 entries, [0] = medium */
+    int32_t tile;             /* 0: global rounds; T > 0: tiled epochs of edge T */
+    int32_t tile_cycles;      /* P_T: tile cycles per MCS (divides P) */
 } orc_params;
 
 /* ------------------------------------------------------------------ */
@@ -581,6 +583,170 @@ static int replay_subpass(const orc_params *p, const orc_tables *tb, int32_t *la
     return 0;
 }
 
+/* ------------------------------------------------------------------ */
+/* Tiled schedule.  Tiles of edge T (a multiple of a) on a grid shifted  */
+/* per MCS by a Philox offset (a multiple of a per axis, counter         */
+/* (0, 0, t, 2<<24), words 0..2 for x, y, z); tile colour = parity of    */
+/* its tile coordinates.  Per MCS, P_T tile cycles visit the 2^d tile    */
+/* colours in a Philox order (swap i from counter (i, cycle, t, 3<<24)). */
+/* In an epoch the tiles of one colour are active; each runs, in order,  */
+/* its 1/P_T share of the MCS's sub-passes (all rounds of each) on the   */
+/* blocks inside it, while the tiles around it are dormant.  Tallies     */
+/* read by a tile are those at the epoch start plus the tile's own       */
+/* changes of earlier rounds.                                            */
+/* ------------------------------------------------------------------ */
+static void tile_offset(const orc_params *p, int64_t t, int64_t off[3])
+{
+    uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
+    uint32_t ctr[4] = {0u, 0u, (uint32_t)t, 2u << 24};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    int units = p->tile / p->a;
+    off[0] = (int64_t)p->a * scale_draw(w[0], (uint32_t)units);
+    off[1] = (int64_t)p->a * scale_draw(w[1], (uint32_t)units);
+    off[2] = p->dim == 3 ? (int64_t)p->a * scale_draw(w[2], (uint32_t)units) : 0;
+}
+
+int orc_tile_colour_perm(const orc_params *p, int64_t t, int cycle, int32_t *perm)
+{
+    int C = p->dim == 3 ? 8 : 4;
+    uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
+    for (int q = 0; q < C; q++) perm[q] = q;
+    for (int i = C - 1; i >= 1; i--) {
+        uint32_t ctr[4] = {(uint32_t)i, (uint32_t)cycle, (uint32_t)t, 3u << 24};
+        uint32_t w[4];
+        orc_philox4x32_10(ctr, key, w);
+        int jj = (int)scale_draw(w[0], (uint32_t)(i + 1));
+        int32_t tmp = perm[i]; perm[i] = perm[jj]; perm[jj] = tmp;
+    }
+    return C;
+}
+
+/* tile coordinate of block coordinate bc along an axis (block edge s) */
+static int64_t tile_of(int64_t bc, int s, int64_t off, int64_t n, int T)
+{
+    int64_t x = bc * s;               /* first site of the block */
+    int64_t u = wrap(x - off, n);     /* shifted coordinate */
+    return u / T;
+}
+
+typedef struct {
+    int32_t si, sj, dAi, dAj;
+} orc_change;
+
+/* One epoch (tile cycle pc_t, tile colour number qt) of MCS t. */
+static int replay_epoch(const orc_params *p, const orc_tables *tb, int32_t *lat, uint8_t *act, int32_t *V,
+                        int32_t *A, int64_t t, int pc_t, int qt, int64_t *accepts)
+{
+    int32_t off[26][3];
+    int nb = orc_neighbour_offsets(p->dim, off);
+    int use_act = act_enabled(p) && act != NULL;
+    int s = p->a / p->c;
+    int C = ipow(p->c, p->dim);
+    int k = ipow(s, p->dim) / p->P;
+    int T = p->tile;
+    int64_t toff[3];
+    tile_offset(p, t, toff);
+    int32_t tperm[8];
+    orc_tile_colour_perm(p, t, pc_t, tperm);
+    int tcol = tperm[qt];
+    int sub_per_epoch = p->P * C / p->tile_cycles;
+    int sp0 = pc_t * sub_per_epoch;
+    int64_t nbx = p->nx / s, nby = p->ny / s, nbz = p->nz / (p->dim == 3 ? s : 1);
+    int64_t ntx = p->nx / T, nty = p->ny / T, ntz = p->dim == 3 ? p->nz / T : 1;
+    int64_t bpt = T / s; /* blocks per tile per axis */
+
+    size_t nv = (size_t)(p->n_cells + 1);
+    int32_t *Vs = (int32_t *)malloc(sizeof(int32_t) * nv);
+    int32_t *As = (int32_t *)malloc(sizeof(int32_t) * nv);
+    int32_t *dV = (int32_t *)calloc(nv, sizeof(int32_t));
+    int32_t *dA = (int32_t *)calloc(nv, sizeof(int32_t));
+    int64_t max_round = 1;
+    for (int d = 0; d < p->dim; d++) max_round *= bpt;
+    orc_change *chg = (orc_change *)malloc(sizeof(orc_change) * (size_t)max_round);
+    int32_t *touched = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * max_round * k * sub_per_epoch + 1));
+    if (!Vs || !As || !dV || !dA || !chg || !touched) {
+        free(Vs); free(As); free(dV); free(dA); free(chg); free(touched);
+        return -1;
+    }
+    memcpy(Vs, V, sizeof(int32_t) * nv);
+    memcpy(As, A, sizeof(int32_t) * nv);
+    int64_t acc = 0;
+    for (int64_t tz = 0; tz < ntz; tz++)
+        for (int64_t ty = 0; ty < nty; ty++)
+            for (int64_t tx = 0; tx < ntx; tx++) {
+                int colour = (int)(tx % 2) + 2 * (int)(ty % 2) + 4 * (int)(tz % 2);
+                if (colour != tcol) continue;
+                int64_t ntouched = 0;
+                for (int sp = sp0; sp < sp0 + sub_per_epoch; sp++) {
+                    int32_t perm[27];
+                    orc_colour_perm(p, t, sp / C, perm);
+                    int col = perm[sp % C];
+                    for (int r = 0; r < k; r++) {
+                        int64_t nchg = 0;
+                        /* blocks of this tile, in tile-local order */
+                        for (int64_t lz = 0; lz < (p->dim == 3 ? bpt : 1); lz++)
+                            for (int64_t ly = 0; ly < bpt; ly++)
+                                for (int64_t lx = 0; lx < bpt; lx++) {
+                                    int64_t bx = wrap(toff[0] / s + tx * bpt + lx, nbx);
+                                    int64_t by = wrap(toff[1] / s + ty * bpt + ly, nby);
+                                    int64_t bz = p->dim == 3 ? wrap(toff[2] / s + tz * bpt + lz, nbz) : 0;
+                                    int bcol = (int)(bx % p->c) + p->c * (int)(by % p->c) +
+                                               p->c * p->c * (int)(bz % p->c);
+                                    if (bcol != col) continue;
+                                    (void)tile_of;
+                                    int64_t b = bx + nbx * (by + nby * bz);
+                                    int64_t j;
+                                    int n;
+                                    uint32_t w2;
+                                    attempt_draw(p, b, r, t, sp, &j, &n, &w2);
+                                    int64_t i = neighbour(p, j, off[n]);
+                                    int32_t si = lat[i], sj = lat[j];
+                                    if (si == sj || si < 0 || sj < 0) continue;
+                                    int64_t Vi = si > 0 ? (int64_t)Vs[si] + dV[si] : 0;
+                                    int64_t Vj = sj > 0 ? (int64_t)Vs[sj] + dV[sj] : 0;
+                                    int64_t Ai = si > 0 ? (int64_t)As[si] + dA[si] : 0;
+                                    int64_t Aj = sj > 0 ? (int64_t)As[sj] + dA[sj] : 0;
+                                    if (sj > 0 && Vj <= 1) continue;
+                                    int mi, mj;
+                                    int64_t dhq = 16 * delta_h_int(p, lat, j, si, sj, Vi, Vj, Ai, Aj, nb, off, &mi, &mj);
+                                    if (use_act) dhq += delta_h_act_q(p, tb, lat, act, i, j, si, sj, nb, off);
+                                    int ok = dhq <= 0 || (dhq < tb->L && w2 < tb->thr[dhq]);
+                                    if (!ok) continue;
+                                    lat[j] = si;
+                                    if (use_act) act[j] = si > 0 ? (uint8_t)p->max_act[type_of(p, si)] : 0;
+                                    chg[nchg].si = si;
+                                    chg[nchg].sj = sj;
+                                    chg[nchg].dAi = nb - 2 * mi;
+                                    chg[nchg].dAj = 2 * mj - nb;
+                                    nchg++;
+                                    acc++;
+                                }
+                        /* the round's changes become visible to the tile's next round */
+                        for (int64_t e = 0; e < nchg; e++) {
+                            if (chg[e].si > 0) {
+                                dV[chg[e].si] += 1; dA[chg[e].si] += chg[e].dAi;
+                                touched[ntouched++] = chg[e].si;
+                            }
+                            if (chg[e].sj > 0) {
+                                dV[chg[e].sj] -= 1; dA[chg[e].sj] += chg[e].dAj;
+                                touched[ntouched++] = chg[e].sj;
+                            }
+                        }
+                    }
+                }
+                /* the tile's changes go into the global tallies; reset its deltas */
+                for (int64_t e = 0; e < ntouched; e++) {
+                    int32_t c = touched[e];
+                    V[c] += dV[c]; A[c] += dA[c];
+                    dV[c] = 0; dA[c] = 0;
+                }
+            }
+    free(Vs); free(As); free(dV); free(dA); free(chg); free(touched);
+    if (accepts) *accepts += acc;
+    return 0;
+}
+
 static int check_params(const orc_params *p)
 {
     if (p->dim != 2 && p->dim != 3) return -1;
@@ -590,11 +756,17 @@ static int check_params(const orc_params *p)
     int s = p->a / p->c;
     if (p->a - s < 2) return -1;
     if (ipow(s, p->dim) % p->P) return -1;
+    if (p->tile) {
+        int T = p->tile;
+        if (T % p->a || p->nx % (2 * T) || p->ny % (2 * T) || (p->dim == 3 && p->nz % (2 * T))) return -1;
+        if (p->tile_cycles < 1 || p->P % p->tile_cycles) return -1;
+    }
     return 0;
 }
 
-/* Advance by n_sub sub-passes from position (t, sp); Act decays at the
- * start of every MCS (sp == 0).  Position is updated in place. */
+/* Advance by n_sub schedule units (sub-passes of the global schedule,
+ * epochs of the tiled one) from position (t, sp); Act decays at the start
+ * of every MCS (sp == 0).  Position is updated in place. */
 int orc_replay_run(const orc_params *p, int32_t *lat, uint8_t *act, int32_t *V, int32_t *A,
                    int64_t *t_io, int32_t *sp_io, int64_t n_sub, int64_t *accepts)
 {
@@ -602,13 +774,16 @@ int orc_replay_run(const orc_params *p, int32_t *lat, uint8_t *act, int32_t *V, 
     orc_tables tb;
     if (tables_init(p, &tb) != 0) return -1;
     int use_act = act_enabled(p) && act != NULL;
-    int per_mcs = p->P * ipow(p->c, p->dim);
+    int CT = p->dim == 3 ? 8 : 4;
+    int per_mcs = p->tile ? p->tile_cycles * CT : p->P * ipow(p->c, p->dim);
     int64_t t = *t_io;
     int32_t sp = *sp_io;
     if (accepts) *accepts = 0;
     for (int64_t it = 0; it < n_sub; it++) {
         if (sp == 0 && use_act) decay_act(p, act);
-        if (replay_subpass(p, &tb, lat, act, V, A, t, sp, accepts) != 0) {
+        int rc = p->tile ? replay_epoch(p, &tb, lat, act, V, A, t, sp / CT, sp % CT, accepts)
+                         : replay_subpass(p, &tb, lat, act, V, A, t, sp, accepts);
+        if (rc != 0) {
             tables_free(&tb);
             return -1;
         }

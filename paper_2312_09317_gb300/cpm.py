@@ -36,6 +36,8 @@ class Config(ctypes.Structure):
         ("init_lattice", ctypes.POINTER(ctypes.c_int32)),
         ("init_act", ctypes.POINTER(ctypes.c_uint8)),
         ("t0", ctypes.c_int64),
+        ("tile", ctypes.c_int32),
+        ("tile_cycles", ctypes.c_int32),
     ]
 
 
@@ -139,6 +141,8 @@ def make_config(w, keep: list) -> Config:
         keep.append(act)
         c.init_act = act.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
     c.t0 = 0
+    c.tile = int(getattr(w, "tile", 0))
+    c.tile_cycles = int(getattr(w, "tile_cycles", 1))
     return c
 
 

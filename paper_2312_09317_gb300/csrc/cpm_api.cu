@@ -20,7 +20,7 @@ struct cpm_handle {
     int dim = 2, nb = 8;
     uint64_t n_sites = 0;
     int32_t n_cells = 0;
-    uint32_t s = 1, C = 1, sd = 1, k = 1, per_mcs = 1;
+    uint32_t s = 1, C = 1, sd = 1, k = 1, per_mcs = 1, per_sub_mcs = 1;
     uint32_t nbx = 1, nby = 1, nbz = 1, n_active = 0;
     bool perim = false, act = false;
     // device state
@@ -35,6 +35,9 @@ struct cpm_handle {
     unsigned long long *counters = nullptr;  // [0] accepts, [1] scratch
     uint8_t *act_tmp = nullptr;
     int32_t L = 0;
+    // tiled schedule
+    uint32_t tile = 0, tile_cycles = 1, CT = 1;
+    int *error_flag = nullptr;
     // position
     int64_t t = 0;
     int32_t sp = 0;
@@ -97,6 +100,7 @@ int validate(const cpm_config *c)
         return fail(nullptr, CPM_E_INVALID, "temperature must be in (0, 2900]");
     if (c->obstacle_type < 1 || c->obstacle_type >= CPM_MAX_TYPES) return fail(nullptr, CPM_E_INVALID, "bad obstacle_type");
     if (c->n_cells < 0 || c->n_cells > (1 << 30)) return fail(nullptr, CPM_E_INVALID, "bad n_cells");
+    if (c->tile > 0 && c->n_cells >= 0x0FFFFFFF) return fail(nullptr, CPM_E_INVALID, "tiled schedule: n_cells < 2^28 - 1");
     if (!c->cell_type || !c->init_lattice) return fail(nullptr, CPM_E_INVALID, "cell_type and init_lattice are required");
     if (c->cell_type[0] != 0) return fail(nullptr, CPM_E_INVALID, "cell_type[0] (medium) must be 0");
     for (int i = 1; i <= c->n_cells; i++)
@@ -110,6 +114,24 @@ int validate(const cpm_config *c)
             return fail(nullptr, CPM_E_INVALID, "lambdas must be >= 0");
     }
     if (c->t0 < 0) return fail(nullptr, CPM_E_INVALID, "t0 must be >= 0");
+    if (c->tile < 0) return fail(nullptr, CPM_E_INVALID, "tile must be >= 0");
+    if (c->tile > 0) {
+        const int T = c->tile;
+        if (T % c->a) return fail(nullptr, CPM_E_INVALID, "tile must be a multiple of a");
+        if ((c->dim == 3 && T > 36) || T > 250) return fail(nullptr, CPM_E_INVALID, "tile edge too large");
+        if (c->nx % (2 * T) || c->ny % (2 * T) || (c->dim == 3 && c->nz % (2 * T)))
+            return fail(nullptr, CPM_E_INVALID, "extents must be multiples of 2*tile");
+        if (c->tile_cycles < 1 || c->P % c->tile_cycles) return fail(nullptr, CPM_E_INVALID, "tile_cycles must divide P");
+        const uint32_t per = (uint32_t)(T / c->a);
+        if (ipow(per, c->dim) > 1024) return fail(nullptr, CPM_E_INVALID, "at most 1024 blocks per tile colour");
+        if ((uint32_t)c->P * ipow(c->c, c->dim) / (uint32_t)c->tile_cycles > (uint32_t)kMaxEpochSubpasses)
+            return fail(nullptr, CPM_E_INVALID, "too many sub-passes per epoch");
+        bool act = false;
+        for (int a = 0; a < CPM_MAX_TYPES; a++)
+            if (c->lambda_act[a]) act = true;
+        if (tile_dyn_smem(c->dim, act, (uint32_t)T, kTileHashCap, (uint32_t)c->a, kTileThrSmem) > 220 * 1024)
+            return fail(nullptr, CPM_E_INVALID, "tile too large for shared memory");
+    }
     for (uint64_t x = 0; x < n; x++) {
         const int32_t v = c->init_lattice[x];
         if (v < -1 || v > c->n_cells) return fail(nullptr, CPM_E_INVALID, "init_lattice[%llu] = %d out of range",
@@ -215,6 +237,101 @@ int run_subpass(cpm_handle *h)
     return CPM_OK;
 }
 
+// Tile grid offset of MCS t: per axis a multiple of a below T, from counter (0, 0, t, 2<<24).
+void tile_offset(const cpm_handle *h, int64_t t, uint32_t off[3])
+{
+    const Philox4 w = philox4x32_10(0u, 0u, (uint32_t)t, 2u << 24, (uint32_t)h->cfg.seed, (uint32_t)(h->cfg.seed >> 32));
+    const uint32_t units = h->tile / (uint32_t)h->cfg.a;
+    off[0] = (uint32_t)h->cfg.a * draw_below(w.v[0], units);
+    off[1] = (uint32_t)h->cfg.a * draw_below(w.v[1], units);
+    off[2] = h->dim == 3 ? (uint32_t)h->cfg.a * draw_below(w.v[2], units) : 0u;
+}
+
+// Tile colour of epoch e of cycle: Fisher-Yates over 2^d colours, swap i from (i, cycle, t, 3<<24).
+uint32_t tile_colour_of(const cpm_handle *h, int64_t t, uint32_t cycle, uint32_t q)
+{
+    uint32_t perm[8];
+    for (uint32_t i = 0; i < h->CT; i++) perm[i] = i;
+    for (uint32_t i = h->CT - 1; i >= 1; i--) {
+        const Philox4 w = philox4x32_10(i, cycle, (uint32_t)t, 3u << 24, (uint32_t)h->cfg.seed,
+                                        (uint32_t)(h->cfg.seed >> 32));
+        const uint32_t j = draw_below(w.v[0], i + 1);
+        const uint32_t tmp = perm[i];
+        perm[i] = perm[j];
+        perm[j] = tmp;
+    }
+    return perm[q];
+}
+
+int run_epoch(cpm_handle *h)
+{
+    if (h->act && h->sp == 0 && h->t % 64 == 0) {
+        CUDA_TRY(h, launch_clamp_stamps(h->stamp, h->n_sites, (uint32_t)h->t, h->stream));
+        h->launches += 1;
+    }
+    const uint32_t cycle = (uint32_t)h->sp / h->CT;
+    const uint32_t tcol = tile_colour_of(h, h->t, cycle, (uint32_t)h->sp % h->CT);
+    const uint32_t n_sub = h->per_sub_mcs / h->tile_cycles;
+    TileArgs a;
+    memset(&a, 0, sizeof a);
+    a.lat = h->lat;
+    a.stamp = h->stamp;
+    a.cell_type = h->cell_type;
+    const int cur = (int)(h->g & 1);
+    a.Vc = V_buf(h, cur);
+    a.Ac = A_buf(h, cur);
+    a.Vn = V_buf(h, cur ^ 1);
+    a.An = A_buf(h, cur ^ 1);
+    a.thr = h->thr;
+    a.ln_tab = h->ln_tab;
+    a.expq = h->expq;
+    a.accepts = h->counters;
+    a.error_flag = h->error_flag;
+    a.L = h->L;
+    a.nx = h->cfg.nx; a.ny = h->cfg.ny; a.nz = h->cfg.nz;
+    a.s = h->s; a.c = h->cfg.c; a.sd = h->sd; a.k = h->k;
+    a.nbx = h->nbx; a.nby = h->nby; a.nbz = h->nbz;
+    a.T = h->tile;
+    a.hash_cap = kTileHashCap;
+    a.thr_smem = (uint32_t)h->L < kTileThrSmem ? (uint32_t)h->L : kTileThrSmem;
+    a.n_sub = n_sub;
+    a.sp0 = cycle * n_sub;
+    a.t = (uint32_t)h->t;
+    a.key0 = (uint32_t)h->cfg.seed;
+    a.key1 = (uint32_t)(h->cfg.seed >> 32);
+    uint32_t off[3];
+    tile_offset(h, h->t, off);
+    a.offx = off[0]; a.offy = off[1]; a.offz = off[2];
+    a.tcx = tcol & 1u; a.tcy = (tcol >> 1) & 1u; a.tcz = (tcol >> 2) & 1u;
+    for (uint32_t q = 0; q < n_sub; q++) a.colours[q] = (int32_t)colour_of(h, h->t, (int32_t)(a.sp0 + q));
+    a.tp = h->tp;
+    const size_t bytes = sizeof(int32_t) * (h->n_cells + 1);
+    CUDA_TRY(h, cudaMemcpyAsync(a.Vn, a.Vc, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(a.An, a.Ac, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    const uint32_t ntx = h->cfg.nx / h->tile, nty = h->cfg.ny / h->tile;
+    const uint32_t ntz = h->dim == 3 ? h->cfg.nz / h->tile : 1;
+    const uint32_t n_tiles = (ntx / 2) * (nty / 2) * (h->dim == 3 ? ntz / 2 : 1);
+    CUDA_TRY(h, launch_tile_epoch(h->dim, h->perim, h->act, a, n_tiles, h->stream));
+    h->launches += 1;
+    h->g += 1;
+    h->attempts += (int64_t)(h->n_sites / ((uint64_t)h->CT * h->tile_cycles));
+    if (++h->sp == (int32_t)h->per_mcs) {
+        h->sp = 0;
+        h->t += 1;
+    }
+    return CPM_OK;
+}
+
+int check_error_flag(cpm_handle *h)
+{
+    if (!h->error_flag) return CPM_OK;
+    int flag = 0;
+    CUDA_TRY(h, cudaMemcpyAsync(&flag, h->error_flag, sizeof flag, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (flag) return fail(h, CPM_E_STATE, "a tile and its halo held more than %u distinct cells", kTileHashCap - 2);
+    return CPM_OK;
+}
+
 int build_tables(cpm_handle *h)
 {
     // THR[h] = min(2^32-1, floor(2^32 exp(-h/(16T)))) up to the first zero
@@ -255,6 +372,7 @@ void free_all(cpm_handle *h)
     cudaFree(h->expq);
     cudaFree(h->counters);
     cudaFree(h->act_tmp);
+    cudaFree(h->error_flag);
 }
 
 int create_impl(cpm_handle *h, const cpm_config *c)
@@ -271,7 +389,12 @@ int create_impl(cpm_handle *h, const cpm_config *c)
     h->C = ipow(c->c, c->dim);
     h->sd = ipow(h->s, c->dim);
     h->k = h->sd / c->P;
-    h->per_mcs = (uint32_t)c->P * h->C;
+    h->per_sub_mcs = (uint32_t)c->P * h->C;
+    h->per_mcs = h->per_sub_mcs;
+    h->tile = (uint32_t)c->tile;
+    h->tile_cycles = c->tile > 0 ? (uint32_t)c->tile_cycles : 1u;
+    h->CT = c->dim == 3 ? 8u : 4u;
+    if (h->tile) h->per_mcs = h->tile_cycles * h->CT;
     h->nbx = c->nx / h->s;
     h->nby = c->ny / h->s;
     h->nbz = c->dim == 3 ? c->nz / h->s : 1;
@@ -298,6 +421,10 @@ int create_impl(cpm_handle *h, const cpm_config *c)
     CUDA_TRY(h, cudaMalloc(&h->tallies, sizeof(int32_t) * nv * 6));
     CUDA_TRY(h, cudaMalloc(&h->pend, sizeof(int4) * 2 * (size_t)h->n_active));
     CUDA_TRY(h, cudaMalloc(&h->counters, sizeof(unsigned long long) * 2));
+    if (h->tile) {
+        CUDA_TRY(h, cudaMalloc(&h->error_flag, sizeof(int)));
+        CUDA_TRY(h, cudaMemsetAsync(h->error_flag, 0, sizeof(int), h->stream));
+    }
     CUDA_TRY(h, cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * 2, h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(h->lat, c->init_lattice, sizeof(int32_t) * h->n_sites, cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(h->cell_type, c->cell_type, nv, cudaMemcpyHostToDevice, h->stream));
@@ -356,7 +483,7 @@ int cpm_step_subpasses(cpm_handle *h, int64_t n)
     if (bad(h)) return CPM_E_HANDLE;
     if (n < 0) return fail(h, CPM_E_INVALID, "n must be >= 0");
     for (int64_t i = 0; i < n; i++) {
-        int rc = run_subpass(h);
+        int rc = h->tile ? run_epoch(h) : run_subpass(h);
         if (rc) return rc;
     }
     return CPM_OK;
@@ -373,6 +500,7 @@ int cpm_read_lattice(cpm_handle *h, int32_t *dst, int dst_is_device)
 {
     if (bad(h)) return CPM_E_HANDLE;
     if (!dst) return fail(h, CPM_E_INVALID, "dst is NULL");
+    if (int rc = check_error_flag(h)) return rc;
     CUDA_TRY(h, cudaMemcpyAsync(dst, h->lat, sizeof(int32_t) * h->n_sites,
                                 dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -382,6 +510,7 @@ int cpm_read_lattice(cpm_handle *h, int32_t *dst, int dst_is_device)
 int cpm_read_tallies(cpm_handle *h, int32_t *V, int32_t *A, int dst_is_device)
 {
     if (bad(h)) return CPM_E_HANDLE;
+    if (int rc = check_error_flag(h)) return rc;
     const int cur = (int)(h->g & 1);
     const size_t bytes = sizeof(int32_t) * (h->n_cells + 1);
     const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;

@@ -90,6 +90,39 @@ struct RoundArgs {
     TypeParams tp;
 };
 
+// Tiled schedule: everything one epoch of one tile colour needs.
+constexpr int kMaxEpochSubpasses = 512;
+constexpr uint32_t kTileHashCap = 512;  // distinct ids a tile and its halo may hold (incl. medium, obstacle)
+constexpr uint32_t kTileThrSmem = 2048;  // threshold-table entries kept in shared memory
+
+struct TileArgs {
+    int32_t *lat;
+    uint8_t *stamp;
+    const uint8_t *cell_type;
+    const int32_t *Vc, *Ac;    // tallies at the start of the epoch (read-only during it)
+    int32_t *Vn, *An;          // copy of Vc/Ac that receives every tile's changes
+    const uint32_t *thr;
+    const int32_t *ln_tab;
+    const int32_t *expq;
+    unsigned long long *accepts;
+    int *error_flag;           // set when a tile's change table overflows
+    int32_t L;
+    uint32_t nx, ny, nz;
+    uint32_t s, c, sd, k;      // block edge, divisions, sites per block, rounds per sub-pass
+    uint32_t nbx, nby, nbz;
+    uint32_t T, hash_cap, thr_smem;
+    uint32_t n_sub, sp0;       // sub-passes of the epoch: sp0 .. sp0 + n_sub - 1
+    uint32_t t;                // MCS (low 32 bits)
+    uint32_t key0, key1;
+    uint32_t offx, offy, offz; // tile grid offset of this MCS
+    uint32_t tcx, tcy, tcz;    // active tile colour, per axis
+    int32_t colours[kMaxEpochSubpasses];
+    TypeParams tp;
+};
+
+size_t tile_dyn_smem(int dim, bool act, uint32_t T, uint32_t cap, uint32_t a, uint32_t thr_smem);
+cudaError_t launch_tile_epoch(int dim, bool perim, bool act, const TileArgs &a, uint32_t n_tiles, cudaStream_t st);
+
 // Launchers (defined in the per-dimension translation units).
 cudaError_t launch_round(int dim, bool perim, bool act, const RoundArgs &a, cudaStream_t st);
 cudaError_t launch_recount(int dim, const int32_t *lat, const uint8_t *cell_type, int32_t *V, int32_t *A,

@@ -110,6 +110,7 @@ extern "C" int cpm_step_noalloc(const cpm_config *cfg, int32_t *lattice, int32_t
     if (t < 0 || sp < 0 || sp >= (int32_t)(C * (uint32_t)c.P) || n_subpasses < 0)
         return na_fail(CPM_E_INVALID, "bad position or count");
     if (!(c.temperature > 0.0)) return na_fail(CPM_E_INVALID, "temperature must be > 0");
+    if (c.tile != 0) return na_fail(CPM_E_INVALID, "only the global schedule (tile = 0) runs here");
 
     // integer tables, on the stack
     uint32_t thr[kNaMaxThr];

@@ -250,3 +250,41 @@ def test_config3_full_size_sampled(cpm):
     changed = int((pre_lat != post_lat).sum())
     assert changed > 0
     sim.close()
+
+
+TILE_CASES = [
+    ("2d_T8_PT1", lambda: cw.random_small(31, dim=2, n=32, n_cells=10, perimeter=True, a=4, c=2, P=4)
+     .replace(tile=8, tile_cycles=1), 4),
+    ("2d_T8_PT4_act_obst", lambda: cw.random_small(32, dim=2, n=32, n_cells=12, perimeter=True, act=True,
+                                                   obstacles=0.06, a=4, c=2, P=4).replace(tile=8, tile_cycles=4), 4),
+    ("2d_T16_PT2_a8", lambda: cw.random_small(33, dim=2, n=64, n_cells=16, edge=5, perimeter=True, act=True,
+                                              a=8, c=2, P=2).replace(tile=16, tile_cycles=2), 3),
+    ("3d_T8_PT1", lambda: cw.random_small(34, dim=3, n=16, n_cells=10, perimeter=True, a=4, c=2, P=8)
+     .replace(tile=8, tile_cycles=1), 2),
+    ("3d_T8_PT2_act_obst", lambda: cw.random_small(35, dim=3, n=16, n_cells=12, perimeter=True, act=True,
+                                                   obstacles=0.05, a=4, c=2, P=8).replace(tile=8, tile_cycles=2), 2),
+    ("3d_tissue_T16", lambda: cw.config3_3d(seed=3, n=64, a=4, c=2, P=8, device="cuda")
+     .replace(tile=16, tile_cycles=1), 2),
+    ("3d_cfg2_T24", lambda: cw.config2_3d(seed=4, n=96, a=4, c=2, P=8).replace(tile=24, tile_cycles=2), 2),
+]
+
+
+@pytest.mark.parametrize("name,factory,n_mcs", TILE_CASES, ids=[c[0] for c in TILE_CASES])
+def test_tiled_schedule_bit_exact(cpm, name, factory, n_mcs):
+    w = factory()
+    sim = cpm.Sim(w)
+    ref = oracle.State(w)
+    for m in range(n_mcs):
+        sim.step(1)
+        ref.replay_run(1)
+        _compare(sim, ref, "tiled %s after MCS %d" % (name, m))
+    # finer steps: single epochs
+    for n in (1, 2, 3):
+        sim.step_subpasses(n)
+        ref.replay_subpasses(n)
+        _compare(sim, ref, "tiled %s after %d more epochs" % (name, n))
+    st = sim.stats()
+    assert (st["mcs"], st["subpass"]) == (ref.t, ref.sp)
+    assert st["attempts"] == ref.t * w.n_sites + ref.sp * w.n_sites // ref.subpasses_per_mcs()
+    assert sim.verify() == 0
+    sim.close()
