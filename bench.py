@@ -37,6 +37,9 @@ UNIT = "attempts/s"
 # Workloads: (factory, algorithmic bytes per site per MCS, description)
 # bytes: int32 lattice read + write (8 B); with Act the uint8 stamp read + write (2 B).
 WORKLOADS = {
+    "cpm2d_200": (lambda: cw.config1_2d(seed=1), 8,
+                  "2D 200x200 Moore-8, 100 one-pixel cells, V_t=100, J(c,c)=20, J(c,m)=10, lambda_V=50, T=20; "
+                  "a=4, c=2, P=1"),
     "cpm3d_256": (lambda: cw.config2_3d(seed=1, n=256, a=4, c=2, P=8), 8,
                   "3D 256^3 Moore-26, ~17,576 cells, V_t=500, A_t=400, lambda_V=25, lambda_P=0.5, "
                   "J(c,c)=20, J(c,m)=12, T=20 (x2 integer scale); a=4, c=2, P=8"),
@@ -56,6 +59,12 @@ WORKLOADS = {
     "cpm3d_tissue_1024_tiled2": (lambda: cw.config3_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda")
                                  .replace(tile=16, tile_cycles=2), 10,
                                  "as cpm3d_tissue_1024, tiled schedule: tiles of edge 16, 2 tile cycles per MCS"),
+    "cpm3d_tissue_1024_t32p8": (lambda: cw.config3_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda")
+                                .replace(tile=32, tile_cycles=8), 10,
+                                "as cpm3d_tissue_1024, tiled schedule: tiles of edge 32, 8 tile cycles per MCS"),
+    "cpm3d_tissue_512_t32p8": (lambda: cw.config3_3d(seed=1, n=512, a=4, c=2, P=8, device="cuda")
+                               .replace(tile=32, tile_cycles=8), 10,
+                               "3D tissue 512^3, tiled schedule: tiles of edge 32, 8 tile cycles per MCS"),
     "cpm3d_tissue_512_tiled": (lambda: cw.config3_3d(seed=1, n=512, a=4, c=2, P=8, device="cuda")
                                .replace(tile=16, tile_cycles=1), 10,
                                "3D tissue 512^3, tiled schedule: tiles of edge 16"),

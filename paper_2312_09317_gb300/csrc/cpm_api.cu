@@ -216,6 +216,7 @@ int run_subpass(cpm_handle *h)
     a.key0 = (uint32_t)h->cfg.seed;
     a.key1 = (uint32_t)(h->cfg.seed >> 32);
     a.tp = h->tp;
+    pick_bricks(h->dim, a.nax, a.nay, a);
     for (uint32_t r = 0; r < h->k; r++) {
         const int cur = (int)(h->g & 1);
         a.r = r;

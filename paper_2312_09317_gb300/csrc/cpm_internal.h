@@ -87,6 +87,7 @@ struct RoundArgs {
     uint32_t cx, cy, cz;       // active colour, per axis
     uint32_t t, sp, r;         // MCS (low 32 bits), sub-pass, round
     uint32_t key0, key1;
+    uint32_t brick_x, brick_y, brick_z;  // active blocks per CTA along each axis (product <= 256)
     TypeParams tp;
 };
 
@@ -122,6 +123,23 @@ struct TileArgs {
 
 size_t tile_dyn_smem(int dim, bool act, uint32_t T, uint32_t cap, uint32_t a, uint32_t thr_smem);
 cudaError_t launch_tile_epoch(int dim, bool perim, bool act, const TileArgs &a, uint32_t n_tiles, cudaStream_t st);
+
+// CTA brick of active blocks for the round kernel: 3D 8x4x4 (128 threads),
+// 2D 16x16; measured on GB300 against other shapes and row-major mapping.
+#ifndef CPM_BRICK3_X
+#define CPM_BRICK3_X 8
+#define CPM_BRICK3_Y 4
+#define CPM_BRICK3_Z 4
+#endif
+inline void pick_bricks(int dim, uint32_t nax, uint32_t nay, RoundArgs &a)
+{
+    if (dim == 3) {
+        a.brick_x = CPM_BRICK3_X; a.brick_y = CPM_BRICK3_Y; a.brick_z = CPM_BRICK3_Z;
+    } else {
+        a.brick_x = 16; a.brick_y = 16; a.brick_z = 1;
+    }
+    (void)nax; (void)nay;
+}
 
 // Launchers (defined in the per-dimension translation units).
 cudaError_t launch_round(int dim, bool perim, bool act, const RoundArgs &a, cudaStream_t st);

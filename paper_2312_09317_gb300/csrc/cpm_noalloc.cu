@@ -172,6 +172,7 @@ extern "C" int cpm_step_noalloc(const cpm_config *cfg, int32_t *lattice, int32_t
     a.n_active = (uint32_t)n_active;
     a.key0 = (uint32_t)c.seed;
     a.key1 = (uint32_t)(c.seed >> 32);
+    pick_bricks(c.dim, a.nax, a.nay, a);
     memcpy(a.tp.J, c.J, sizeof a.tp.J);
     memcpy(a.tp.lambda_v, c.lambda_v, sizeof a.tp.lambda_v);
     memcpy(a.tp.v_target, c.v_target, sizeof a.tp.v_target);
