@@ -55,6 +55,15 @@ CASES = [
                                             obstacles=0.05, a=8, c=2, P=64), 2),
     ("3d_a8_P2", lambda: cw.random_small(10, dim=3, n=16, n_cells=10, edge=4, perimeter=True, act=True,
                                          a=8, c=2, P=2), 2),
+    # larger 3D lattices; 44 and 52 give CTA bricks (8 x 4 x 4 active blocks) that overhang the active grid
+    ("3d_staged_adh_vol", lambda: cw.random_small(41, dim=3, n=48, n_cells=40, edge=5, perimeter=False,
+                                                  a=4, c=2, P=8), 2),
+    ("3d_staged_act_obst", lambda: cw.random_small(42, dim=3, n=48, n_cells=40, edge=5, perimeter=True, act=True,
+                                                   obstacles=0.05, a=4, c=2, P=1), 2),
+    ("3d_staged_ragged44", lambda: cw.random_small(43, dim=3, n=44, n_cells=30, edge=5, perimeter=True, act=True,
+                                                   a=4, c=2, P=2), 2),
+    ("3d_staged_ragged52", lambda: cw.random_small(44, dim=3, n=52, n_cells=30, edge=5, perimeter=True,
+                                                   obstacles=0.03, a=4, c=2, P=8), 2),
 ]
 
 
