@@ -69,6 +69,16 @@ WORKLOADS = {
                                .replace(tile=16, tile_cycles=1), 10,
                                "3D tissue 512^3, tiled schedule: tiles of edge 16"),
 }
+# Ensembles (config 4): many independent lattices of uneven sizes advanced
+# together; a step is one MCS of every member.
+ENSEMBLES = {
+    "cpm_ensemble_512": (lambda: cw.ensemble(512, seed=1),
+                         "512 lattices (2D 64^2..512^2, 3D 64^3..128^3, log-uniform), 10..2,000 cells each, "
+                         "J(c,c), J(c,m), lambda_V, lambda_P, lambda_act, Max_act, T from a Latin hypercube "
+                         "(x10 integer scale); a=4, c=2, one round per colour visit; 2D and 3D members in two "
+                         "batches on one stream"),
+}
+
 DEFAULT_WORKLOAD = "cpm3d_tissue_1024"
 
 # DRAM bytes per round-kernel launch from the last ncu capture, valid only for
@@ -217,7 +227,10 @@ def run_reference(args):
     ws, rank, local, dist = dist_init()
     if rank != 0:
         return 0
-    w_full = WORKLOADS[args.workload][0]()
+    if args.workload in ENSEMBLES:
+        w_full = ENSEMBLES[args.workload][0]()[0]
+    else:
+        w_full = WORKLOADS[args.workload][0]()
     w = crop(w_full)
     import oracle
     st = oracle.State(w)
@@ -371,13 +384,121 @@ def run_gpu(args):
     return 0
 
 
+def run_gpu_batch(args):
+    import torch
+    from paper_2312_09317_gb300 import build as B
+    from paper_2312_09317_gb300 import cpm
+
+    ws_, rank, local, dist = dist_init()
+    torch.cuda.set_device(local)
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    barrier(dist)
+    factory, desc = ENSEMBLES[args.workload]
+    members = [w.replace(seed=w.seed + 1000003 * rank) for w in factory()]
+    stream = torch.cuda.Stream()
+    groups = [[w for w in members if w.dim == d] for d in (2, 3)]
+    batches = [cpm.Batch(g, stream=stream) for g in groups if g]
+    n = sum(w.n_sites for w in members)
+    alg_bytes = sum((10 if w.act_on else 8) * w.n_sites for w in members)
+    rounds = sum(max((w.a // w.c) ** w.dim * w.c ** w.dim for w in g) for g in groups if g)
+    for _ in range(args.warmup):
+        for b in batches:
+            b.step(1)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    l0 = sum(b.launches() for b in batches)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(dist)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            ev[k][0].record(stream)
+            for b in batches:
+                b.step(1)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    clk = clocks.stop()
+    launches = sum(b.launches() for b in batches) - l0
+    t_local = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    t_max = max_over_ranks(dist, t_local)
+    value = sum_over_ranks(dist, float(args.steps * n)) / t_max
+    step_s = t_local / args.steps
+    launch_ms = 1e3 * step_s / max(1, launches // args.steps)
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / step_s / 1e9
+
+    # end to end: every member's lattice in from pinned host memory, one MCS, every lattice out
+    hosts = []
+    for b in batches:
+        for k, w in enumerate(b.ws):
+            h = torch.empty((w.nz, w.ny, w.nx), dtype=torch.int32, pin_memory=True).numpy()
+            b.read_lattice(k, h)
+            hosts.append((b, k, h))
+    e2e_steps = max(2, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for b, k, h in hosts:
+            b.load_lattice(k, h)
+        for b in batches:
+            b.step(1)
+        for b, k, h in hosts:
+            b.read_lattice(k, h)
+    e2e_t = max_over_ranks(dist, time.perf_counter() - t0)
+    e2e_value = sum_over_ranks(dist, float(e2e_steps * n)) / e2e_t
+
+    cpu = None
+    if rank == 0 and ws_ == 1 and not args.no_cpu_baseline:
+        import oracle
+        t_used, att, used = 0.0, 0, 0
+        for w in members:
+            if t_used >= args.cpu_budget:
+                break
+            st = oracle.State(w)
+            t0 = time.perf_counter()
+            st.serial_run(1)
+            t_used += time.perf_counter() - t0
+            att += w.n_sites
+            used += 1
+        cpu = {"value": att / t_used, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "serial CPM oracle (a), one thread, the first MCS of the first %d ensemble members "
+                         "(%.1f s)" % (used, t_used)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws_, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "members": len(members), "sites": n,
+                       "launches_per_step": launches // args.steps, "l2": "inputs larger than L2",
+                       "parallelism": "replicas" if ws_ > 1 else "1 GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": "of %s" % peak_kind,
+                         "kernel": "batch_round_kernel", "launch_ms": launch_ms,
+                         "alg_bytes_per_launch": alg_bytes / max(1, launches // args.steps)},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n,
+                    "steps": e2e_steps},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    for b in batches:
+        b.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + sorted(ENSEMBLES))
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -385,6 +506,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in ENSEMBLES:
+        return run_gpu_batch(args)
     return run_gpu(args)
 
 

@@ -332,3 +332,77 @@ def random_small(seed: int, dim: int = 2, n: int = 16, n_cells: int = 6, edge: i
     nz = 1 if dim == 2 else n
     return Workload("random_small_%dd_%d" % (dim, seed), dim, n, n, nz, J, lv, vt, lp, at, la,
                     ma, float(T), 1, a, c, P, seed, obstacle_type, lat, ct, actv, 1)
+
+
+# --------------------------------------------------------------------------
+# config 4: an ensemble for parameter sweeps
+# --------------------------------------------------------------------------
+
+SWEEP_RANGES = {            # the seven swept parameters, in model units
+    "J_cc": (5.0, 40.0),
+    "J_cm": (2.0, 25.0),
+    "lambda_V": (5.0, 100.0),
+    "lambda_P": (0.0, 2.0),
+    "lambda_act": (0.0, 400.0),
+    "max_act": (10.0, 60.0),
+    "T": (5.0, 40.0),
+}
+SWEEP_SCALE = 10            # integer energy scale S for the swept parameters
+
+
+def latin_hypercube(n: int, rng) -> dict:
+    """n points of a Latin hypercube over SWEEP_RANGES: every parameter's
+    range is cut into n strata, each used once, in an independent random
+    order, with a uniform position inside the stratum."""
+    out = {}
+    for k, (lo, hi) in SWEEP_RANGES.items():
+        u = (rng.permutation(n) + rng.random(n)) / n
+        out[k] = lo + (hi - lo) * u
+    return out
+
+
+def ensemble(n: int = 512, seed: int = 1, dim: Optional[int] = None, side2=(64, 512), side3=(64, 128),
+             cells=(10, 2000), a: int = 4, c: int = 2) -> list:
+    """Config 4: n lattices of uneven sizes (log-uniform edge, 2D or 3D),
+    10..2000 cells each, parameters from a Latin hypercube (SWEEP_RANGES,
+    scaled by SWEEP_SCALE).  Targets: V_t = half the lattice per cell (at
+    least 10 sites); A_t = 1.2x an estimate of a compact cell's interface
+    count (12.5 sqrt(V) in 2D with 8 neighbours, 45 V^(2/3) in 3D with 26).
+    Cells start as squares / cubes of edge 3 at jittered-grid centres."""
+    rng = np.random.default_rng(seed)
+    hc = latin_hypercube(n, rng)
+    S = SWEEP_SCALE
+    out = []
+    for k in range(n):
+        d = dim if dim is not None else int(rng.integers(2, 4))
+        lo, hi = side2 if d == 2 else side3
+        side = int(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+        side = max(8 * a, (side // (2 * a)) * (2 * a))
+        shape = (side,) * d
+        n_sites = side ** d
+        nc = int(np.exp(rng.uniform(np.log(cells[0]), np.log(cells[1]))))
+        nc = max(1, min(nc, n_sites // 64))
+        spacing = (n_sites / nc) ** (1.0 / d)
+        lat = np.zeros(shape, dtype=np.int32)
+        ctr = jittered_centres(shape, spacing, max(0.0, spacing / 2 - 2), rng)
+        ctr = ctr[rng.permutation(len(ctr))][:nc]
+        ncell = place_cubes(lat, ctr, 3)
+        J, lv, vt, lp, at, la, ma = _params()
+        _sym(J, 1, 1, int(round(hc["J_cc"][k] * S)))
+        _sym(J, 1, 0, int(round(hc["J_cm"][k] * S)))
+        lv[1] = int(round(hc["lambda_V"][k] * S))
+        v_t = max(10, int(0.5 * n_sites / max(ncell, 1)))
+        vt[1] = v_t
+        lp[1] = int(round(hc["lambda_P"][k] * S))
+        at[1] = int(round(1.2 * (12.5 * v_t ** 0.5 if d == 2 else 45.0 * v_t ** (2.0 / 3.0))))
+        la[1] = int(round(hc["lambda_act"][k] * S))
+        ma[1] = int(round(hc["max_act"][k]))
+        ct = np.ones(ncell + 1, dtype=np.uint8)
+        ct[0] = 0
+        if d == 2:
+            lat = lat[None]
+        P = (a // c) ** d  # one round per colour visit
+        out.append(Workload("ensemble_%d_%dd_%d" % (k, d, side), d, side, side, 1 if d == 2 else side, J, lv, vt,
+                            lp, at, la, ma, float(hc["T"][k] * S), S, a, c, P, seed * 100003 + k, 2, lat, ct,
+                            None, 1000))
+    return out

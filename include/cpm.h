@@ -179,6 +179,47 @@ const char *cpm_last_error(const cpm_handle *h);
 /* Free every resource of h (NULL is ignored).  Synchronises the stream. */
 void cpm_destroy(cpm_handle *h);
 
+/* Batched ensembles (many independent lattices, e.g. replicates or a
+ * parameter sweep, advanced together; the paper runs ensembles as
+ * independent simulations, Results, "Serial Cellular Potts Models are
+ * limited", Fig. 1B).  Every lattice of a batch is a full simulation with its
+ * own configuration and seed; after cpm_batch_step(b, n) lattice i is
+ * exactly what cpm_step(h_i, n) gives for a handle created from cfgs[i].  A
+ * batch step launches one kernel per round for all lattices that still have
+ * rounds in the call (lattices with fewer rounds per MCS finish earlier).
+ * All configurations of a batch must share dim and use the global schedule
+ * (tile = 0).  The library owns all device memory; cfgs is borrowed for the
+ * duration of cpm_batch_create. */
+typedef struct cpm_batch cpm_batch;
+
+/* Create n lattices from cfgs[0..n-1] on cuda_stream.  Errors as cpm_create
+ * (the message names the offending configuration). */
+int cpm_batch_create(const cpm_config *cfgs, int32_t n, void *cuda_stream, cpm_batch **out);
+
+/* Advance every lattice by n_mcs MCS (asynchronous on the batch's stream). */
+int cpm_batch_step(cpm_batch *b, int64_t n_mcs);
+
+/* Number of lattices in b (0 for NULL). */
+int32_t cpm_batch_size(const cpm_batch *b);
+
+/* Per-lattice access, as cpm_read_lattice, cpm_load_lattice, cpm_read_tallies,
+ * cpm_read_act and cpm_stats for lattice idx (0 <= idx < n). */
+int cpm_batch_read_lattice(cpm_batch *b, int32_t idx, int32_t *dst, int dst_is_device);
+int cpm_batch_load_lattice(cpm_batch *b, int32_t idx, const int32_t *src, int src_is_device);
+int cpm_batch_read_tallies(cpm_batch *b, int32_t idx, int32_t *V, int32_t *A, int dst_is_device);
+int cpm_batch_read_act(cpm_batch *b, int32_t idx, uint8_t *dst, int dst_is_device);
+int cpm_batch_stats(cpm_batch *b, int32_t idx, cpm_stats_t *out);
+
+/* Kernel launches issued for b (set-up included). */
+int64_t cpm_batch_kernel_launches(const cpm_batch *b);
+
+/* Message of the last failed call on b (of the last failed cpm_batch_create
+ * when b is NULL). */
+const char *cpm_batch_last_error(const cpm_batch *b);
+
+/* Free b and all its lattices (NULL is ignored).  Synchronises the stream. */
+void cpm_batch_destroy(cpm_batch *b);
+
 /* cpm_step_noalloc -- the sweep without any device allocation.
  *
  * The paper has no counterpart: this entry point exists for callers that

@@ -67,6 +67,19 @@ _SIGNATURES = {
     "cpm_kernel_launches": (ctypes.c_int64, [ctypes.c_void_p]),
     "cpm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "cpm_destroy": (None, [ctypes.c_void_p]),
+    "cpm_batch_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int32, ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "cpm_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "cpm_batch_size": (ctypes.c_int32, [ctypes.c_void_p]),
+    "cpm_batch_read_lattice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int]),
+    "cpm_batch_load_lattice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int]),
+    "cpm_batch_read_tallies": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_int]),
+    "cpm_batch_read_act": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int]),
+    "cpm_batch_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(Stats)]),
+    "cpm_batch_kernel_launches": (ctypes.c_int64, [ctypes.c_void_p]),
+    "cpm_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "cpm_batch_destroy": (None, [ctypes.c_void_p]),
     "cpm_step_noalloc": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
@@ -214,6 +227,80 @@ class Sim:
         if getattr(self, "h", None) is not None and self.h.value:
             self.lib.cpm_destroy(self.h)
             self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """An ensemble of independent lattices advanced together (a cpm_batch)."""
+
+    def __init__(self, workloads, stream=None):
+        lib = load()
+        self.ws = list(workloads)
+        keep: list = []
+        arr = (Config * len(self.ws))()
+        for k, w in enumerate(self.ws):
+            arr[k] = make_config(w, keep)
+        b = ctypes.c_void_p()
+        st = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+        rc = lib.cpm_batch_create(arr, len(self.ws), ctypes.c_void_p(st), ctypes.byref(b))
+        if rc != CPM_OK:
+            raise CPMError(rc, lib.cpm_batch_last_error(None).decode())
+        self.b = b
+        self.lib = lib
+
+    def _check(self, rc):
+        if rc != CPM_OK:
+            raise CPMError(rc, self.lib.cpm_batch_last_error(self.b).decode())
+
+    def __len__(self):
+        return int(self.lib.cpm_batch_size(self.b))
+
+    def step(self, n_mcs: int = 1):
+        self._check(self.lib.cpm_batch_step(self.b, n_mcs))
+
+    def read_lattice(self, idx: int, out=None):
+        w = self.ws[idx]
+        if out is None:
+            out = np.empty((w.nz, w.ny, w.nx), dtype=np.int32)
+        p, dev = _ptr(out)
+        self._check(self.lib.cpm_batch_read_lattice(self.b, idx, ctypes.c_void_p(p), dev))
+        return out
+
+    def load_lattice(self, idx: int, src):
+        p, dev = _ptr(src)
+        self._check(self.lib.cpm_batch_load_lattice(self.b, idx, ctypes.c_void_p(p), dev))
+
+    def read_tallies(self, idx: int):
+        w = self.ws[idx]
+        V = np.empty(w.n_cells + 1, dtype=np.int32)
+        A = np.empty(w.n_cells + 1, dtype=np.int32)
+        self._check(self.lib.cpm_batch_read_tallies(self.b, idx, ctypes.c_void_p(V.ctypes.data),
+                                                    ctypes.c_void_p(A.ctypes.data), 0))
+        return V, A
+
+    def read_act(self, idx: int):
+        w = self.ws[idx]
+        out = np.empty((w.nz, w.ny, w.nx), dtype=np.uint8)
+        self._check(self.lib.cpm_batch_read_act(self.b, idx, ctypes.c_void_p(out.ctypes.data), 0))
+        return out
+
+    def stats(self, idx: int) -> dict:
+        s = Stats()
+        self._check(self.lib.cpm_batch_stats(self.b, idx, ctypes.byref(s)))
+        return s.as_dict()
+
+    def launches(self) -> int:
+        return int(self.lib.cpm_batch_kernel_launches(self.b))
+
+    def close(self):
+        if getattr(self, "b", None) is not None and self.b.value:
+            self.lib.cpm_batch_destroy(self.b)
+            self.b = ctypes.c_void_p()
 
     def __del__(self):
         try:

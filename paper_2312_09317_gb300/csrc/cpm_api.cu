@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -615,6 +616,240 @@ void cpm_destroy(cpm_handle *h)
     cudaStreamSynchronize(h->stream);
     free_all(h);
     delete h;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batched ensembles: many independent lattices advanced by shared launches.
+// Each lattice is a full handle (its own buffers, tables, position); a batch
+// step runs round q of every lattice that still has rounds left in the call,
+// with one kernel launch for all of them.
+// ===========================================================================
+struct cpm_batch {
+    std::vector<cpm_handle *> hs;
+    int dim = 2;
+    bool perim = false, act = false;
+    cudaStream_t stream = nullptr;
+    std::vector<BatchLattice> lats;      // in batch order
+    std::vector<uint32_t> order;         // lattice indices by rounds per MCS, descending
+    std::vector<uint32_t> items_upto;    // items of the first k lattices in that order
+    BatchLattice *d_lats = nullptr;
+    int2 *d_items = nullptr;
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+std::string g_batch_create_error;
+
+int bfail(cpm_batch *b, int code, const std::string &msg)
+{
+    if (b) b->err = msg; else g_batch_create_error = msg;
+    return code;
+}
+
+void batch_free(cpm_batch *b)
+{
+    for (cpm_handle *h : b->hs) cpm_destroy(h);
+    cudaFree(b->d_lats);
+    cudaFree(b->d_items);
+}
+}  // namespace
+
+extern "C" {
+
+int cpm_batch_create(const cpm_config *cfgs, int32_t n, void *cuda_stream, cpm_batch **out)
+{
+    if (!out) return bfail(nullptr, CPM_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!cfgs || n < 1) return bfail(nullptr, CPM_E_INVALID, "need at least one configuration");
+    cpm_batch *b = new (std::nothrow) cpm_batch();
+    if (!b) return bfail(nullptr, CPM_E_NOMEM, "host allocation failed");
+    b->stream = (cudaStream_t)cuda_stream;
+    b->dim = cfgs[0].dim;
+    for (int32_t i = 0; i < n; i++) {
+        if (cfgs[i].dim != b->dim || cfgs[i].tile != 0) {
+            batch_free(b);
+            delete b;
+            return bfail(nullptr, CPM_E_INVALID, "a batch needs one dimension and the global schedule (tile = 0)");
+        }
+        cpm_handle *h = nullptr;
+        int rc = cpm_create(&cfgs[i], cuda_stream, &h);
+        if (rc) {
+            std::string msg = "configuration " + std::to_string(i) + ": " + cpm_last_error(nullptr);
+            batch_free(b);
+            delete b;
+            return bfail(nullptr, rc, msg);
+        }
+        b->hs.push_back(h);
+        b->perim |= h->perim;
+        b->act |= h->act;
+    }
+    // per-lattice descriptors
+    for (cpm_handle *h : b->hs) {
+        BatchLattice L;
+        memset(&L, 0, sizeof L);
+        RoundArgs &a = L.base;
+        a.lat = h->lat;
+        a.stamp = h->stamp;
+        a.cell_type = h->cell_type;
+        a.thr = h->thr;
+        a.ln_tab = h->ln_tab;
+        a.expq = h->expq;
+        a.accepts = h->counters;
+        a.L = h->L;
+        a.nx = h->cfg.nx; a.ny = h->cfg.ny; a.nz = h->cfg.nz;
+        a.s = h->s; a.c = h->cfg.c; a.sd = h->sd;
+        a.nbx = h->nbx; a.nby = h->nby;
+        a.nax = h->nbx / h->cfg.c; a.nay = h->nby / h->cfg.c;
+        a.n_active = h->n_active;
+        a.key0 = (uint32_t)h->cfg.seed;
+        a.key1 = (uint32_t)(h->cfg.seed >> 32);
+        a.tp = h->tp;
+        for (int p = 0; p < 2; p++) {
+            L.V[p] = V_buf(h, p);
+            L.A[p] = A_buf(h, p);
+            L.pend[p] = h->pend + (size_t)p * h->n_active;
+        }
+        L.k = h->k;
+        L.C = h->C;
+        L.R = h->per_sub_mcs * h->k;
+        b->lats.push_back(L);
+    }
+    b->order.resize(n);
+    for (int32_t i = 0; i < n; i++) b->order[i] = (uint32_t)i;
+    std::stable_sort(b->order.begin(), b->order.end(),
+                     [&](uint32_t x, uint32_t y) { return b->lats[x].R > b->lats[y].R; });
+    std::vector<int2> items;
+    b->items_upto.push_back(0);
+    for (uint32_t l : b->order) {
+        const uint32_t chunks = (b->hs[l]->n_active + kBatchThreads - 1) / kBatchThreads;
+        for (uint32_t c = 0; c < chunks; c++) items.push_back(make_int2((int)l, (int)c));
+        b->items_upto.push_back((uint32_t)items.size());
+    }
+    cudaError_t e = cudaMalloc(&b->d_lats, sizeof(BatchLattice) * b->lats.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(int2) * std::max<size_t>(items.size(), 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        batch_free(b);
+        delete b;
+        return bfail(nullptr, e == cudaErrorMemoryAllocation ? CPM_E_NOMEM : CPM_E_CUDA, cudaGetErrorString(e));
+    }
+    *out = b;
+    return CPM_OK;
+}
+
+int cpm_batch_step(cpm_batch *b, int64_t n_mcs)
+{
+    if (!b) return CPM_E_HANDLE;
+    if (n_mcs < 0) return bfail(b, CPM_E_INVALID, "n_mcs must be >= 0");
+    if (n_mcs == 0) return CPM_OK;
+    for (size_t l = 0; l < b->hs.size(); l++) {
+        if (b->hs[l]->sp != 0) return bfail(b, CPM_E_INVALID, "every lattice must be at an MCS boundary");
+        b->lats[l].t_start = b->hs[l]->t;
+        b->lats[l].g_start = b->hs[l]->g;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_lats, b->lats.data(), sizeof(BatchLattice) * b->lats.size(),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return bfail(b, CPM_E_CUDA, cudaGetErrorString(e));
+    const uint64_t r_max = b->lats[b->order[0]].R;
+    const uint64_t Q = (uint64_t)n_mcs * r_max;
+    size_t active = b->order.size();  // lattices (in order) that still have rounds at step q
+    for (uint64_t q = 0; q < Q; q++) {
+        while (active > 0 && (uint64_t)n_mcs * b->lats[b->order[active - 1]].R <= q) active--;
+        if (b->act) {
+            for (size_t k = 0; k < active; k++) {
+                const uint32_t l = b->order[k];
+                cpm_handle *h = b->hs[l];
+                const uint64_t R = b->lats[l].R;
+                if (!h->act || q % R) continue;
+                const int64_t t = h->t + (int64_t)(q / R);
+                if (t % 64) continue;
+                e = launch_clamp_stamps(h->stamp, h->n_sites, (uint32_t)t, b->stream);
+                if (e != cudaSuccess) return bfail(b, CPM_E_CUDA, cudaGetErrorString(e));
+                b->launches += 1;
+            }
+        }
+        e = launch_batch_round(b->dim, b->perim, b->act, b->d_lats, b->d_items, b->items_upto[active], (uint32_t)q,
+                               b->stream);
+        if (e != cudaSuccess) return bfail(b, CPM_E_CUDA, cudaGetErrorString(e));
+        b->launches += 1;
+    }
+    for (size_t l = 0; l < b->hs.size(); l++) {
+        cpm_handle *h = b->hs[l];
+        h->t += n_mcs;
+        h->g += (uint64_t)n_mcs * b->lats[l].R;
+        h->attempts += n_mcs * (int64_t)h->n_sites;
+    }
+    return CPM_OK;
+}
+
+int32_t cpm_batch_size(const cpm_batch *b) { return b ? (int32_t)b->hs.size() : 0; }
+
+int cpm_batch_read_lattice(cpm_batch *b, int32_t idx, int32_t *dst, int dst_is_device)
+{
+    if (!b) return CPM_E_HANDLE;
+    if (idx < 0 || idx >= (int32_t)b->hs.size()) return bfail(b, CPM_E_INVALID, "lattice index out of range");
+    int rc = cpm_read_lattice(b->hs[idx], dst, dst_is_device);
+    if (rc) b->err = cpm_last_error(b->hs[idx]);
+    return rc;
+}
+
+int cpm_batch_load_lattice(cpm_batch *b, int32_t idx, const int32_t *src, int src_is_device)
+{
+    if (!b) return CPM_E_HANDLE;
+    if (idx < 0 || idx >= (int32_t)b->hs.size()) return bfail(b, CPM_E_INVALID, "lattice index out of range");
+    int rc = cpm_load_lattice(b->hs[idx], src, src_is_device);
+    if (rc) b->err = cpm_last_error(b->hs[idx]);
+    return rc;
+}
+
+int cpm_batch_read_tallies(cpm_batch *b, int32_t idx, int32_t *V, int32_t *A, int dst_is_device)
+{
+    if (!b) return CPM_E_HANDLE;
+    if (idx < 0 || idx >= (int32_t)b->hs.size()) return bfail(b, CPM_E_INVALID, "lattice index out of range");
+    int rc = cpm_read_tallies(b->hs[idx], V, A, dst_is_device);
+    if (rc) b->err = cpm_last_error(b->hs[idx]);
+    return rc;
+}
+
+int cpm_batch_read_act(cpm_batch *b, int32_t idx, uint8_t *dst, int dst_is_device)
+{
+    if (!b) return CPM_E_HANDLE;
+    if (idx < 0 || idx >= (int32_t)b->hs.size()) return bfail(b, CPM_E_INVALID, "lattice index out of range");
+    int rc = cpm_read_act(b->hs[idx], dst, dst_is_device);
+    if (rc) b->err = cpm_last_error(b->hs[idx]);
+    return rc;
+}
+
+int cpm_batch_stats(cpm_batch *b, int32_t idx, cpm_stats_t *out)
+{
+    if (!b) return CPM_E_HANDLE;
+    if (idx < 0 || idx >= (int32_t)b->hs.size()) return bfail(b, CPM_E_INVALID, "lattice index out of range");
+    int rc = cpm_stats(b->hs[idx], out);
+    if (rc) b->err = cpm_last_error(b->hs[idx]);
+    return rc;
+}
+
+int64_t cpm_batch_kernel_launches(const cpm_batch *b)
+{
+    if (!b) return 0;
+    int64_t n = b->launches;
+    for (const cpm_handle *h : b->hs) n += h->launches;
+    return n;
+}
+
+const char *cpm_batch_last_error(const cpm_batch *b) { return b ? b->err.c_str() : g_batch_create_error.c_str(); }
+
+void cpm_batch_destroy(cpm_batch *b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    batch_free(b);
+    delete b;
 }
 
 }  // extern "C"

@@ -91,6 +91,22 @@ struct RoundArgs {
     TypeParams tp;
 };
 
+// Batched ensembles: one lattice of the batch.  base carries its buffers and
+// constants (per-round fields are filled in by the kernel); the round of
+// lattice l at batch step q is round g_start + q of that lattice, in MCS
+// t_start + q / R.
+constexpr uint32_t kBatchThreads = 128;
+struct BatchLattice {
+    RoundArgs base;
+    int32_t *V[2], *A[2];
+    int4 *pend[2];
+    uint32_t R, k, C, pad_;
+    int64_t t_start;
+    uint64_t g_start;
+};
+cudaError_t launch_batch_round(int dim, bool perim, bool act, const BatchLattice *lats, const int2 *items,
+                               uint32_t n_items, uint32_t q, cudaStream_t st);
+
 // Tiled schedule: everything one epoch of one tile colour needs.
 constexpr int kMaxEpochSubpasses = 512;
 constexpr uint32_t kTileHashCap = 512;  // distinct ids a tile and its halo may hold (incl. medium, obstacle)

@@ -107,34 +107,15 @@ __device__ __forceinline__ int64_t floor_div_pos(int64_t num, int64_t den)
     return q;
 }
 
-// Four resident CTAs per SM (at most 64 registers a thread): the round kernel
-// is latency-bound, and the Act variant gains ~40% over 128 registers.
-#ifndef CPM_ROUND_MIN_BLOCKS
-#define CPM_ROUND_MIN_BLOCKS 4
-#endif
-
+// One copy attempt of active block (ix, iy, iz) (active index i) in the round
+// described by a; also carries the previous round's change of index i into
+// the next tallies.  Returns whether the copy was accepted.
 template <int DIM, bool PERIM, bool ACT>
-__global__ void __launch_bounds__(kThreads, CPM_ROUND_MIN_BLOCKS) round_kernel(const RoundArgs a)
+__device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTables &sm, uint32_t ix, uint32_t iy,
+                                              uint32_t iz, uint32_t i)
 {
-    __shared__ SmemTables sm;
-    load_tables(sm, a, ACT);
-    __syncthreads();
-
     constexpr int NB = DIM == 3 ? 26 : 8;
-    // each CTA covers a brick of bx_ x by_ x bz_ active blocks, so that the
-    // stencils of its threads overlap in L1
-    const uint32_t bx_ = a.brick_x, by_ = a.brick_y, bz_ = DIM == 3 ? a.brick_z : 1;
-    const uint32_t nbrx = (a.nax + bx_ - 1) / bx_, nbry = (a.nay + by_ - 1) / by_;
-    const uint32_t brick = blockIdx.x;
-    const uint32_t tx = threadIdx.x % bx_, ty = (threadIdx.x / bx_) % by_, tz = threadIdx.x / (bx_ * by_);
-    const uint32_t ix = (brick % nbrx) * bx_ + tx;
-    const uint32_t iy = ((brick / nbrx) % nbry) * by_ + ty;
-    const uint32_t iz = (brick / (nbrx * nbry)) * bz_ + tz;
-    const uint32_t naz = a.n_active / (a.nax * a.nay);
-    const bool valid = threadIdx.x < bx_ * by_ * bz_ && ix < a.nax && iy < a.nay && iz < naz;
-    const uint32_t i = ix + a.nax * (iy + a.nay * iz);
     bool accepted = false;
-    if (valid) {
         // the previous round's accepted change goes into the next tallies
         const int4 e = a.pend_prev[i];
         if (e.x != e.y) {
@@ -218,7 +199,7 @@ __global__ void __launch_bounds__(kThreads, CPM_ROUND_MIN_BLOCKS) round_kernel(c
                 const bool ok = dhq <= 0 || (dhq < a.L && w.v[2] < __ldg(a.thr + dhq));
                 if (ok) {
                     a.lat[j] = si;
-                    if (ACT) a.stamp[j] = (uint8_t)(si > 0 ? (a.t & 255u) : ((a.t - 128u) & 255u));
+                    if (ACT && a.stamp) a.stamp[j] = (uint8_t)(si > 0 ? (a.t & 255u) : ((a.t - 128u) & 255u));
                     if (si > 0) { atomicAdd(a.Vn + si, 1); atomicAdd(a.An + si, dAi); }
                     if (sj > 0) { atomicAdd(a.Vn + sj, -1); atomicAdd(a.An + sj, dAj); }
                     out = make_int4(si, sj, dAi, dAj);
@@ -227,9 +208,95 @@ __global__ void __launch_bounds__(kThreads, CPM_ROUND_MIN_BLOCKS) round_kernel(c
             }
         }
         a.pend_cur[i] = out;
+    return accepted;
+}
+
+// Four resident CTAs per SM (at most 64 registers a thread): the round kernel
+// is latency-bound, and the Act variant gains ~40% over 128 registers.
+#ifndef CPM_ROUND_MIN_BLOCKS
+#define CPM_ROUND_MIN_BLOCKS 4
+#endif
+
+template <int DIM, bool PERIM, bool ACT>
+__global__ void __launch_bounds__(kThreads, CPM_ROUND_MIN_BLOCKS) round_kernel(const RoundArgs a)
+{
+    __shared__ SmemTables sm;
+    load_tables(sm, a, ACT);
+    __syncthreads();
+
+    // each CTA covers a brick of bx_ x by_ x bz_ active blocks, so that the
+    // stencils of its threads overlap in L1
+    const uint32_t bx_ = a.brick_x, by_ = a.brick_y, bz_ = DIM == 3 ? a.brick_z : 1;
+    const uint32_t nbrx = (a.nax + bx_ - 1) / bx_, nbry = (a.nay + by_ - 1) / by_;
+    const uint32_t brick = blockIdx.x;
+    const uint32_t tx = threadIdx.x % bx_, ty = (threadIdx.x / bx_) % by_, tz = threadIdx.x / (bx_ * by_);
+    const uint32_t ix = (brick % nbrx) * bx_ + tx;
+    const uint32_t iy = ((brick / nbrx) % nbry) * by_ + ty;
+    const uint32_t iz = (brick / (nbrx * nbry)) * bz_ + tz;
+    const uint32_t naz = a.n_active / (a.nax * a.nay);
+    const bool valid = threadIdx.x < bx_ * by_ * bz_ && ix < a.nax && iy < a.nay && iz < naz;
+    const uint32_t i = ix + a.nax * (iy + a.nay * iz);
+    bool accepted = false;
+    if (valid) {
+        accepted = round_attempt<DIM, PERIM, ACT>(a, sm, ix, iy, iz, i);
     }
     const unsigned m = __ballot_sync(0xffffffffu, accepted);
     if ((threadIdx.x & 31) == 0 && m != 0) atomicAdd(a.accepts, (unsigned long long)__popc(m));
+}
+
+// Batched round: every CTA takes one (lattice, chunk of 128 active blocks)
+// item and runs that lattice's round number g_start + q, exactly as the
+// single-lattice round kernel would (same colour, counters and tallies).
+template <int DIM, bool PERIM, bool ACT>
+__global__ void __launch_bounds__(kBatchThreads, CPM_ROUND_MIN_BLOCKS)
+    batch_round_kernel(const BatchLattice *lats, const int2 *items, uint32_t q)
+{
+    __shared__ RoundArgs ra;
+    __shared__ SmemTables sm;
+    const int2 it = items[blockIdx.x];
+    if (threadIdx.x == 0) {
+        const BatchLattice &L = lats[it.x];
+        ra = L.base;
+        const uint64_t t = (uint64_t)L.t_start + q / L.R;
+        const uint32_t mm = q % L.R;
+        const uint32_t sp = mm / L.k, r = mm % L.k;
+        // colour: Fisher-Yates over the C colours of cycle sp / C, swap i from counter (i, cycle, t, 1<<24)
+        uint32_t perm[27];
+        for (uint32_t c = 0; c < L.C; ++c) perm[c] = c;
+        for (uint32_t k = L.C - 1; k >= 1; --k) {
+            const Philox4 w = philox4x32_10(k, sp / L.C, (uint32_t)t, 1u << 24, ra.key0, ra.key1);
+            const uint32_t j = draw_below(w.v[0], k + 1);
+            const uint32_t tmp = perm[k];
+            perm[k] = perm[j];
+            perm[j] = tmp;
+        }
+        const uint32_t col = perm[sp % L.C];
+        ra.cx = col % ra.c;
+        ra.cy = (col / ra.c) % ra.c;
+        ra.cz = col / (ra.c * ra.c);
+        ra.t = (uint32_t)t;
+        ra.sp = sp;
+        ra.r = r;
+        const uint32_t par = (uint32_t)((L.g_start + q) & 1u);
+        ra.Vc = L.V[par];
+        ra.Ac = L.A[par];
+        ra.Vn = L.V[par ^ 1u];
+        ra.An = L.A[par ^ 1u];
+        ra.pend_prev = L.pend[par ^ 1u];
+        ra.pend_cur = L.pend[par];
+    }
+    __syncthreads();
+    load_tables(sm, ra, ACT);
+    __syncthreads();
+    const uint32_t i = (uint32_t)it.y * blockDim.x + threadIdx.x;
+    bool accepted = false;
+    if (i < ra.n_active) {
+        const uint32_t ix = i % ra.nax, rest = i / ra.nax;
+        const uint32_t iy = rest % ra.nay, iz = rest / ra.nay;
+        accepted = round_attempt<DIM, PERIM, ACT>(ra, sm, ix, iy, iz, i);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, accepted);
+    if ((threadIdx.x & 31) == 0 && m != 0) atomicAdd(ra.accepts, (unsigned long long)__popc(m));
 }
 
 template <int DIM>
@@ -314,6 +381,30 @@ cudaError_t launch_round(int dim, bool perim, bool act, const RoundArgs &a, cuda
     }
     if (act) return perim ? launch_round_t<3, true, true>(a, st) : launch_round_t<3, false, true>(a, st);
     return perim ? launch_round_t<3, true, false>(a, st) : launch_round_t<3, false, false>(a, st);
+}
+
+cudaError_t launch_batch_round(int dim, bool perim, bool act, const BatchLattice *lats, const int2 *items,
+                               uint32_t n_items, uint32_t q, cudaStream_t st)
+{
+    if (n_items == 0) return cudaSuccess;
+    if (dim == 2) {
+        if (act) {
+            if (perim) batch_round_kernel<2, true, true><<<n_items, kBatchThreads, 0, st>>>(lats, items, q);
+            else batch_round_kernel<2, false, true><<<n_items, kBatchThreads, 0, st>>>(lats, items, q);
+        } else {
+            if (perim) batch_round_kernel<2, true, false><<<n_items, kBatchThreads, 0, st>>>(lats, items, q);
+            else batch_round_kernel<2, false, false><<<n_items, kBatchThreads, 0, st>>>(lats, items, q);
+        }
+    } else {
+        if (act) {
+            if (perim) batch_round_kernel<3, true, true><<<n_items, kBatchThreads, 0, st>>>(lats, items, q);
+            else batch_round_kernel<3, false, true><<<n_items, kBatchThreads, 0, st>>>(lats, items, q);
+        } else {
+            if (perim) batch_round_kernel<3, true, false><<<n_items, kBatchThreads, 0, st>>>(lats, items, q);
+            else batch_round_kernel<3, false, false><<<n_items, kBatchThreads, 0, st>>>(lats, items, q);
+        }
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_recount(int dim, const int32_t *lat, const uint8_t *, int32_t *V, int32_t *A, uint32_t nx,
