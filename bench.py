@@ -402,6 +402,8 @@ def run_gpu_batch(args):
     n = sum(w.n_sites for w in members)
     alg_bytes = sum((10 if w.act_on else 8) * w.n_sites for w in members)
     rounds = sum(max((w.a // w.c) ** w.dim * w.c ** w.dim for w in g) for g in groups if g)
+    # the autotuner times its CTA shapes on the batches themselves (untimed; it only changes the split)
+    choices = [b.autotune(2) for b in batches]
     for _ in range(args.warmup):
         for b in batches:
             b.step(1)
@@ -472,7 +474,8 @@ def run_gpu_batch(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "members": len(members), "sites": n,
-                       "launches_per_step": launches // args.steps, "l2": "inputs larger than L2",
+                       "launches_per_step": launches // args.steps, "autotuned_shapes": choices,
+                       "l2": "inputs larger than L2",
                        "parallelism": "replicas" if ws_ > 1 else "1 GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": "of %s" % peak_kind,

@@ -196,8 +196,20 @@ typedef struct cpm_batch cpm_batch;
  * (the message names the offending configuration). */
 int cpm_batch_create(const cpm_config *cfgs, int32_t n, void *cuda_stream, cpm_batch **out);
 
-/* Advance every lattice by n_mcs MCS (asynchronous on the batch's stream). */
+/* Advance every lattice by n_mcs MCS (asynchronous on the batch's stream).
+ * One MCS of the whole batch is a CUDA graph, captured on first use: the Act
+ * stamp clamp, one launch per round over the members that still have
+ * rounds, and a device-side advance of every member's MCS counter. */
 int cpm_batch_step(cpm_batch *b, int64_t n_mcs);
+
+/* Pick the CTA brick shape (active blocks per CTA along x, y, z) for this
+ * batch by timing: in 1 + n_mcs_each passes every candidate shape runs one
+ * MCS of the batch itself (the first pass only warms up) and the shape
+ * with the least total time is kept.  The shape changes only how the work
+ * is split over CTAs, never the result, so the batch simply advances by
+ * candidates * (1 + n_mcs_each) MCS (7 candidates in 3D, 6 in 2D).
+ * *choice (if not NULL) receives the chosen candidate's number. */
+int cpm_batch_autotune(cpm_batch *b, int32_t n_mcs_each, int32_t *choice);
 
 /* Number of lattices in b (0 for NULL). */
 int32_t cpm_batch_size(const cpm_batch *b);

@@ -71,6 +71,7 @@ _SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_void_p)]),
     "cpm_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "cpm_batch_size": (ctypes.c_int32, [ctypes.c_void_p]),
+    "cpm_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "cpm_batch_read_lattice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int]),
     "cpm_batch_load_lattice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int]),
     "cpm_batch_read_tallies": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
@@ -259,6 +260,12 @@ class Batch:
 
     def __len__(self):
         return int(self.lib.cpm_batch_size(self.b))
+
+    def autotune(self, n_mcs_each: int = 2) -> int:
+        """Time the candidate CTA shapes on this batch (it advances) and keep the fastest."""
+        k = ctypes.c_int32(-1)
+        self._check(self.lib.cpm_batch_autotune(self.b, n_mcs_each, ctypes.byref(k)))
+        return k.value
 
     def step(self, n_mcs: int = 1):
         self._check(self.lib.cpm_batch_step(self.b, n_mcs))

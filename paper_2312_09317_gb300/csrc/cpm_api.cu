@@ -631,11 +631,18 @@ struct cpm_batch {
     int dim = 2;
     bool perim = false, act = false;
     cudaStream_t stream = nullptr;
+    cudaStream_t capture_stream = nullptr;
     std::vector<BatchLattice> lats;      // in batch order
     std::vector<uint32_t> order;         // lattice indices by rounds per MCS, descending
-    std::vector<uint32_t> items_upto;    // items of the first k lattices in that order
+    std::vector<uint32_t> items_upto;    // round items of the first k lattices in that order
+    uint32_t n_clamp_items = 0;
+    uint32_t brick[3] = {8, 4, 4};       // active blocks per CTA (x, y, z)
     BatchLattice *d_lats = nullptr;
     int2 *d_items = nullptr;
+    int2 *d_clamp = nullptr;
+    cudaGraphExec_t graph = nullptr;     // one MCS of every member
+    int64_t graph_launches = 0;          // kernels in one replay
+    bool descriptors_dirty = true;
     int64_t launches = 0;
     std::string err;
 };
@@ -649,11 +656,102 @@ int bfail(cpm_batch *b, int code, const std::string &msg)
     return code;
 }
 
+void batch_drop_graph(cpm_batch *b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
 void batch_free(cpm_batch *b)
 {
+    batch_drop_graph(b);
     for (cpm_handle *h : b->hs) cpm_destroy(h);
     cudaFree(b->d_lats);
     cudaFree(b->d_items);
+    cudaFree(b->d_clamp);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+}
+
+uint32_t batch_threads(const cpm_batch *b) { return b->brick[0] * b->brick[1] * (b->dim == 3 ? b->brick[2] : 1); }
+
+// round items (member, brick) for the current brick shape, members in order of
+// rounds per MCS (descending), and the Act clamp items (member, 65,536 sites)
+int batch_build_items(cpm_batch *b)
+{
+    std::vector<int2> items;
+    b->items_upto.assign(1, 0);
+    const uint32_t bz = b->dim == 3 ? b->brick[2] : 1;
+    for (uint32_t l : b->order) {
+        const cpm_handle *h = b->hs[l];
+        const uint32_t nax = h->nbx / h->cfg.c, nay = h->nby / h->cfg.c;
+        const uint32_t naz = h->n_active / (nax * nay);
+        const uint32_t nb = ((nax + b->brick[0] - 1) / b->brick[0]) * ((nay + b->brick[1] - 1) / b->brick[1]) *
+                            ((naz + bz - 1) / bz);
+        for (uint32_t c = 0; c < nb; c++) items.push_back(make_int2((int)l, (int)c));
+        b->items_upto.push_back((uint32_t)items.size());
+        b->lats[l].base.brick_x = b->brick[0];
+        b->lats[l].base.brick_y = b->brick[1];
+        b->lats[l].base.brick_z = bz;
+    }
+    std::vector<int2> clamp;
+    for (size_t l = 0; l < b->hs.size(); l++) {
+        if (!b->hs[l]->act) continue;
+        const uint64_t chunks = (b->hs[l]->n_sites + 65535) / 65536;
+        for (uint64_t c = 0; c < chunks; c++) clamp.push_back(make_int2((int)l, (int)c));
+    }
+    b->n_clamp_items = (uint32_t)clamp.size();
+    cudaFree(b->d_items);
+    cudaFree(b->d_clamp);
+    b->d_items = nullptr;
+    b->d_clamp = nullptr;
+    cudaError_t e = cudaMalloc(&b->d_items, sizeof(int2) * std::max<size_t>(items.size(), 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_clamp, sizeof(int2) * std::max<size_t>(clamp.size(), 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !clamp.empty())
+        e = cudaMemcpy(b->d_clamp, clamp.data(), sizeof(int2) * clamp.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bfail(b, CPM_E_CUDA, cudaGetErrorString(e));
+    b->descriptors_dirty = true;
+    batch_drop_graph(b);
+    return CPM_OK;
+}
+
+// Capture one MCS of every member as a CUDA graph: the Act clamp (members at
+// a multiple of 64 MCS), R_max round launches over the members that still
+// have rounds, and the advance of every member's MCS and round counters.
+int batch_build_graph(cpm_batch *b)
+{
+    batch_drop_graph(b);
+    cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bfail(b, CPM_E_CUDA, cudaGetErrorString(e));
+    int64_t n = 0;
+    if (b->act) {
+        e = launch_batch_clamp(b->d_lats, b->d_clamp, b->n_clamp_items, b->capture_stream);
+        n++;
+    }
+    const uint32_t r_max = b->lats[b->order[0]].R;
+    size_t active = b->order.size();
+    for (uint32_t q = 0; q < r_max && e == cudaSuccess; q++) {
+        while (active > 0 && b->lats[b->order[active - 1]].R <= q) active--;
+        e = launch_batch_round(b->dim, b->perim, b->act, b->d_lats, b->d_items, b->items_upto[active], q,
+                               batch_threads(b), b->capture_stream);
+        n++;
+    }
+    if (e == cudaSuccess) {
+        e = launch_batch_advance(b->d_lats, (uint32_t)b->lats.size(), b->capture_stream);
+        n++;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->capture_stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return bfail(b, CPM_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    b->graph_launches = n;
+    return CPM_OK;
 }
 }  // namespace
 
@@ -668,6 +766,7 @@ int cpm_batch_create(const cpm_config *cfgs, int32_t n, void *cuda_stream, cpm_b
     if (!b) return bfail(nullptr, CPM_E_NOMEM, "host allocation failed");
     b->stream = (cudaStream_t)cuda_stream;
     b->dim = cfgs[0].dim;
+    if (b->dim == 2) { b->brick[0] = 16; b->brick[1] = 8; b->brick[2] = 1; }
     for (int32_t i = 0; i < n; i++) {
         if (cfgs[i].dim != b->dim || cfgs[i].tile != 0) {
             batch_free(b);
@@ -686,7 +785,6 @@ int cpm_batch_create(const cpm_config *cfgs, int32_t n, void *cuda_stream, cpm_b
         b->perim |= h->perim;
         b->act |= h->act;
     }
-    // per-lattice descriptors
     for (cpm_handle *h : b->hs) {
         BatchLattice L;
         memset(&L, 0, sizeof L);
@@ -721,22 +819,19 @@ int cpm_batch_create(const cpm_config *cfgs, int32_t n, void *cuda_stream, cpm_b
     for (int32_t i = 0; i < n; i++) b->order[i] = (uint32_t)i;
     std::stable_sort(b->order.begin(), b->order.end(),
                      [&](uint32_t x, uint32_t y) { return b->lats[x].R > b->lats[y].R; });
-    std::vector<int2> items;
-    b->items_upto.push_back(0);
-    for (uint32_t l : b->order) {
-        const uint32_t chunks = (b->hs[l]->n_active + kBatchThreads - 1) / kBatchThreads;
-        for (uint32_t c = 0; c < chunks; c++) items.push_back(make_int2((int)l, (int)c));
-        b->items_upto.push_back((uint32_t)items.size());
-    }
     cudaError_t e = cudaMalloc(&b->d_lats, sizeof(BatchLattice) * b->lats.size());
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(int2) * std::max<size_t>(items.size(), 1));
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         batch_free(b);
         delete b;
         return bfail(nullptr, e == cudaErrorMemoryAllocation ? CPM_E_NOMEM : CPM_E_CUDA, cudaGetErrorString(e));
+    }
+    int rc = batch_build_items(b);
+    if (rc) {
+        std::string msg = b->err;
+        batch_free(b);
+        delete b;
+        return bfail(nullptr, rc, msg);
     }
     *out = b;
     return CPM_OK;
@@ -747,43 +842,79 @@ int cpm_batch_step(cpm_batch *b, int64_t n_mcs)
     if (!b) return CPM_E_HANDLE;
     if (n_mcs < 0) return bfail(b, CPM_E_INVALID, "n_mcs must be >= 0");
     if (n_mcs == 0) return CPM_OK;
-    for (size_t l = 0; l < b->hs.size(); l++) {
-        if (b->hs[l]->sp != 0) return bfail(b, CPM_E_INVALID, "every lattice must be at an MCS boundary");
-        b->lats[l].t_start = b->hs[l]->t;
-        b->lats[l].g_start = b->hs[l]->g;
-    }
-    cudaError_t e = cudaMemcpyAsync(b->d_lats, b->lats.data(), sizeof(BatchLattice) * b->lats.size(),
-                                    cudaMemcpyHostToDevice, b->stream);
-    if (e != cudaSuccess) return bfail(b, CPM_E_CUDA, cudaGetErrorString(e));
-    const uint64_t r_max = b->lats[b->order[0]].R;
-    const uint64_t Q = (uint64_t)n_mcs * r_max;
-    size_t active = b->order.size();  // lattices (in order) that still have rounds at step q
-    for (uint64_t q = 0; q < Q; q++) {
-        while (active > 0 && (uint64_t)n_mcs * b->lats[b->order[active - 1]].R <= q) active--;
-        if (b->act) {
-            for (size_t k = 0; k < active; k++) {
-                const uint32_t l = b->order[k];
-                cpm_handle *h = b->hs[l];
-                const uint64_t R = b->lats[l].R;
-                if (!h->act || q % R) continue;
-                const int64_t t = h->t + (int64_t)(q / R);
-                if (t % 64) continue;
-                e = launch_clamp_stamps(h->stamp, h->n_sites, (uint32_t)t, b->stream);
-                if (e != cudaSuccess) return bfail(b, CPM_E_CUDA, cudaGetErrorString(e));
-                b->launches += 1;
-            }
+    if (b->descriptors_dirty) {
+        for (size_t l = 0; l < b->hs.size(); l++) {
+            if (b->hs[l]->sp != 0) return bfail(b, CPM_E_INVALID, "every lattice must be at an MCS boundary");
+            b->lats[l].t_start = b->hs[l]->t;
+            b->lats[l].g_start = b->hs[l]->g;
         }
-        e = launch_batch_round(b->dim, b->perim, b->act, b->d_lats, b->d_items, b->items_upto[active], (uint32_t)q,
-                               b->stream);
+        cudaError_t e = cudaMemcpyAsync(b->d_lats, b->lats.data(), sizeof(BatchLattice) * b->lats.size(),
+                                        cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
         if (e != cudaSuccess) return bfail(b, CPM_E_CUDA, cudaGetErrorString(e));
-        b->launches += 1;
+        b->descriptors_dirty = false;
     }
+    if (!b->graph) {
+        int rc = batch_build_graph(b);
+        if (rc) return rc;
+    }
+    for (int64_t k = 0; k < n_mcs; k++) {
+        cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+        if (e != cudaSuccess) return bfail(b, CPM_E_CUDA, cudaGetErrorString(e));
+    }
+    b->launches += n_mcs * b->graph_launches;
     for (size_t l = 0; l < b->hs.size(); l++) {
         cpm_handle *h = b->hs[l];
         h->t += n_mcs;
         h->g += (uint64_t)n_mcs * b->lats[l].R;
         h->attempts += n_mcs * (int64_t)h->n_sites;
     }
+    return CPM_OK;
+}
+
+int cpm_batch_autotune(cpm_batch *b, int32_t n_mcs_each, int32_t *choice)
+{
+    if (!b) return CPM_E_HANDLE;
+    if (n_mcs_each < 1) return bfail(b, CPM_E_INVALID, "n_mcs_each must be >= 1");
+    static const uint32_t cand3[][3] = {{8, 4, 4}, {4, 4, 4}, {8, 8, 4}, {16, 4, 2}, {32, 4, 1}, {128, 1, 1}, {8, 8, 2}};
+    static const uint32_t cand2[][3] = {{16, 8, 1}, {16, 16, 1}, {8, 8, 1}, {32, 4, 1}, {128, 1, 1}, {64, 4, 1}};
+    const int nc = b->dim == 3 ? 7 : 6;
+    std::vector<float> total(nc, 0.0f);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = CPM_OK;
+    // passes interleave the candidates, so that each is timed on a similar
+    // spread of simulation states (the cost of an MCS drifts as cells grow)
+    for (int pass = 0; pass < 1 + n_mcs_each && rc == CPM_OK; pass++) {
+        for (int k = 0; k < nc && rc == CPM_OK; k++) {
+            const uint32_t *cb = b->dim == 3 ? cand3[k] : cand2[k];
+            b->brick[0] = cb[0]; b->brick[1] = cb[1]; b->brick[2] = cb[2];
+            rc = batch_build_items(b);
+            if (!rc) rc = cpm_batch_step(b, 0);
+            if (!rc && !b->graph) rc = batch_build_graph(b);
+            if (rc) break;
+            // a freshly built graph is uploaded on its first launch: pass 0 only warms up
+            cudaEventRecord(e0, b->stream);
+            rc = cpm_batch_step(b, 1);
+            cudaEventRecord(e1, b->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (pass > 0) total[k] += ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    int best_k = 0;
+    for (int k = 1; k < nc; k++)
+        if (total[k] < total[best_k]) best_k = k;
+    const uint32_t *cb = b->dim == 3 ? cand3[best_k] : cand2[best_k];
+    b->brick[0] = cb[0]; b->brick[1] = cb[1]; b->brick[2] = cb[2];
+    rc = batch_build_items(b);
+    if (rc) return rc;
+    if (choice) *choice = best_k;
     return CPM_OK;
 }
 

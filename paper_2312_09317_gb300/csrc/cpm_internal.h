@@ -95,7 +95,7 @@ struct RoundArgs {
 // constants (per-round fields are filled in by the kernel); the round of
 // lattice l at batch step q is round g_start + q of that lattice, in MCS
 // t_start + q / R.
-constexpr uint32_t kBatchThreads = 128;
+constexpr uint32_t kBatchMaxThreads = 256;
 struct BatchLattice {
     RoundArgs base;
     int32_t *V[2], *A[2];
@@ -105,7 +105,9 @@ struct BatchLattice {
     uint64_t g_start;
 };
 cudaError_t launch_batch_round(int dim, bool perim, bool act, const BatchLattice *lats, const int2 *items,
-                               uint32_t n_items, uint32_t q, cudaStream_t st);
+                               uint32_t n_items, uint32_t q, uint32_t threads, cudaStream_t st);
+cudaError_t launch_batch_clamp(const BatchLattice *lats, const int2 *items, uint32_t n_items, cudaStream_t st);
+cudaError_t launch_batch_advance(BatchLattice *lats, uint32_t n, cudaStream_t st);
 
 // Tiled schedule: everything one epoch of one tile colour needs.
 constexpr int kMaxEpochSubpasses = 512;

@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kThreads, CPM_ROUND_MIN_BLOCKS) round_kernel(c
 // item and runs that lattice's round number g_start + q, exactly as the
 // single-lattice round kernel would (same colour, counters and tallies).
 template <int DIM, bool PERIM, bool ACT>
-__global__ void __launch_bounds__(kBatchThreads, CPM_ROUND_MIN_BLOCKS)
+__global__ void __launch_bounds__(kBatchMaxThreads, 2)
     batch_round_kernel(const BatchLattice *lats, const int2 *items, uint32_t q)
 {
     __shared__ RoundArgs ra;
@@ -288,11 +288,18 @@ __global__ void __launch_bounds__(kBatchThreads, CPM_ROUND_MIN_BLOCKS)
     __syncthreads();
     load_tables(sm, ra, ACT);
     __syncthreads();
-    const uint32_t i = (uint32_t)it.y * blockDim.x + threadIdx.x;
+    // brick it.y of bx x by x bz active blocks (bricks in x-fastest order)
+    const uint32_t bx_ = ra.brick_x, by_ = ra.brick_y, bz_ = DIM == 3 ? ra.brick_z : 1;
+    const uint32_t nbrx = (ra.nax + bx_ - 1) / bx_, nbry = (ra.nay + by_ - 1) / by_;
+    const uint32_t brick = (uint32_t)it.y;
+    const uint32_t tx = threadIdx.x % bx_, ty = (threadIdx.x / bx_) % by_, tz = threadIdx.x / (bx_ * by_);
+    const uint32_t ix = (brick % nbrx) * bx_ + tx;
+    const uint32_t iy = ((brick / nbrx) % nbry) * by_ + ty;
+    const uint32_t iz = (brick / (nbrx * nbry)) * bz_ + tz;
+    const uint32_t naz = ra.n_active / (ra.nax * ra.nay);
     bool accepted = false;
-    if (i < ra.n_active) {
-        const uint32_t ix = i % ra.nax, rest = i / ra.nax;
-        const uint32_t iy = rest % ra.nay, iz = rest / ra.nay;
+    if (threadIdx.x < bx_ * by_ * bz_ && ix < ra.nax && iy < ra.nay && iz < naz) {
+        const uint32_t i = ix + ra.nax * (iy + ra.nay * iz);
         accepted = round_attempt<DIM, PERIM, ACT>(ra, sm, ix, iy, iz, i);
     }
     const unsigned m = __ballot_sync(0xffffffffu, accepted);
@@ -383,10 +390,49 @@ cudaError_t launch_round(int dim, bool perim, bool act, const RoundArgs &a, cuda
     return perim ? launch_round_t<3, true, false>(a, st) : launch_round_t<3, false, false>(a, st);
 }
 
-cudaError_t launch_batch_round(int dim, bool perim, bool act, const BatchLattice *lats, const int2 *items,
-                               uint32_t n_items, uint32_t q, cudaStream_t st)
+// Act stamp clamp for every member whose MCS t_start is a multiple of 64
+// (run at the start of its MCS); items are (member, chunk of 65,536 sites).
+__global__ void batch_clamp_kernel(const BatchLattice *lats, const int2 *items)
+{
+    const int2 it = items[blockIdx.x];
+    const BatchLattice &L = lats[it.x];
+    if (L.base.stamp == nullptr || (L.t_start % 64) != 0) return;
+    const uint64_t n = (uint64_t)L.base.nx * L.base.ny * L.base.nz;
+    const uint32_t t8 = (uint32_t)L.t_start & 255u;
+    const uint64_t lo = (uint64_t)it.y * 65536u, hi = lo + 65536u < n ? lo + 65536u : n;
+    for (uint64_t x = lo + threadIdx.x; x < hi; x += blockDim.x) {
+        const uint32_t age = (t8 - (uint32_t)L.base.stamp[x]) & 255u;
+        if (age >= 128u) L.base.stamp[x] = (uint8_t)((t8 - 128u) & 255u);
+    }
+}
+
+// End of one batch MCS: every member moves to its next MCS.
+__global__ void batch_advance_kernel(BatchLattice *lats, uint32_t n)
+{
+    for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+        lats[l].t_start += 1;
+        lats[l].g_start += lats[l].R;
+    }
+}
+
+cudaError_t launch_batch_clamp(const BatchLattice *lats, const int2 *items, uint32_t n_items, cudaStream_t st)
 {
     if (n_items == 0) return cudaSuccess;
+    batch_clamp_kernel<<<n_items, 256, 0, st>>>(lats, items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_advance(BatchLattice *lats, uint32_t n, cudaStream_t st)
+{
+    batch_advance_kernel<<<(n + 255) / 256, 256, 0, st>>>(lats, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_round(int dim, bool perim, bool act, const BatchLattice *lats, const int2 *items,
+                               uint32_t n_items, uint32_t q, uint32_t threads, cudaStream_t st)
+{
+    if (n_items == 0) return cudaSuccess;
+    const uint32_t kBatchThreads = threads;
     if (dim == 2) {
         if (act) {
             if (perim) batch_round_kernel<2, true, true><<<n_items, kBatchThreads, 0, st>>>(lats, items, q);

@@ -92,3 +92,20 @@ def test_batch_rejects_mixed_dimensions(cpm):
     ws = [cw.random_small(1, dim=2, n=16, n_cells=3), cw.random_small(2, dim=3, n=12, n_cells=3)]
     with pytest.raises(cpm.CPMError):
         cpm.Batch(ws)
+
+
+def test_batch_autotune_keeps_results_exact(cpm):
+    """The autotuner runs every candidate CTA shape on the batch itself; the
+    members must still follow the replay exactly (3D: 7 shapes x 2 passes)."""
+    ws = [cw.random_small(300 + k, dim=3, n=[16, 24][k % 2], n_cells=6 + k, edge=3, perimeter=True,
+                          act=bool(k % 2), a=4, c=2, P=8) for k in range(4)]
+    batch = cpm.Batch(ws)
+    refs = [oracle.State(w) for w in ws]
+    batch.step(1)
+    choice = batch.autotune(1)
+    assert 0 <= choice < 7
+    batch.step(2)
+    for r in refs:
+        r.replay_run(1 + 7 * 2 + 2)
+    _check(batch, refs, "after autotune")
+    batch.close()
