@@ -79,6 +79,17 @@ ENSEMBLES = {
                          "batches on one stream"),
 }
 
+# The emulator (config 5): sweep points answered at <= 5% error on the summary
+# statistics, emulator + CPM fallback against the CPM alone.
+EMULATOR = {
+    "emulator_sweep": "MLP-ensemble emulator (5 x 7-256x4-16, GELU, bf16/fp32) of 16 summary statistics of 2D "
+                      "64x64 runs with 16 cells (V_t=128), J(c,c), J(c,m), lambda_V, lambda_P, lambda_act, "
+                      "Max_act, T from a Latin hypercube (x10 integer scale); 200 MCS burn-in + 800 MCS observed "
+                      "every 10 MCS; trained on batched-CPM runs (80/20 split); fallback when the ensemble std "
+                      "exceeds 3x the validation RMSE",
+}
+SWEEP_METRIC = "sweep points/s at <=5% stat error"
+
 DEFAULT_WORKLOAD = "cpm3d_tissue_1024"
 
 # DRAM bytes per round-kernel launch from the last ncu capture, valid only for
@@ -103,6 +114,16 @@ def peaks():
         d = json.load(open(p))
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def peaks_bf16():
+    """Dense bf16 tensor peak (TFLOP/s): the measured cuBLAS burst figure, else the fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        if "bf16_tflops" in d:
+            return float(d["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
 
 
 class ClockSampler:
@@ -227,6 +248,8 @@ def run_reference(args):
     ws, rank, local, dist = dist_init()
     if rank != 0:
         return 0
+    if args.workload in EMULATOR:
+        return run_reference_sweep(args, ws)
     if args.workload in ENSEMBLES:
         w_full = ENSEMBLES[args.workload][0]()[0]
     else:
@@ -253,6 +276,37 @@ def run_reference(args):
                                    % (args.steps, args.warmup, "a %d^3 crop of the workload" % w.nx
                                       if w is not w_full else "the whole workload")},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_reference_sweep(args, ws):
+    """The sweep answered by the serial CPM oracle alone: each step runs one
+    emulator-geometry run (64x64, 16 cells) for a bounded number of MCS and
+    extrapolates to the full 1,000 MCS of a sweep run; one run per point, so
+    the figure is an upper bound on the CPU's sweep points/s at any error."""
+    import oracle
+    mcs = 20
+    times = []
+    X = cw.sweep_points(args.warmup + args.steps, 5)
+    for k in range(args.warmup + args.steps):
+        st = oracle.State(cw.emulator_run(X[k], 9000 + k))
+        t0 = time.perf_counter()
+        st.serial_run(mcs)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    per_run = sum(times) / len(times) * (1000.0 / mcs)
+    value = 1.0 / per_run
+    line = {
+        "impl": "reference", "metric": SWEEP_METRIC, "value": value, "unit": "points/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_run, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 (serial CPM)", "data": "synthetic",
+        "config": {"workload": args.workload, "description": EMULATOR[args.workload]},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle",
+                         "sample": "serial CPM oracle (a), one thread: %d MCS of each of %d emulator runs, "
+                                   "extrapolated to 1,000 MCS per run, one run per sweep point" % (mcs, args.steps)},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
@@ -495,13 +549,151 @@ def run_gpu_batch(args):
     return 0
 
 
+def run_emulator_sweep(args):
+    """Config 5: train the emulator on batched-CPM runs, measure its error
+    against replicate means of the CPM at held-out points, then time sweeps
+    answered by emulator + CPM fallback against the CPM alone (batched, and
+    one lattice at a time), both at <= 5% error on the same statistics."""
+    import torch
+    from paper_2312_09317_gb300 import build as B
+    from paper_2312_09317_gb300 import cpm
+    from paper_2312_09317_gb300 import emulator as em
+
+    ws_, rank, local, dist = dist_init()
+    torch.cuda.set_device(local)
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    barrier(dist)
+    cpm.load()
+    burn, window, every = 200, 800, 10
+    sim = dict(burn=burn, window=window, every=every)
+    N = args.emu_runs
+    seed0 = 1 + 7919 * rank
+    # 1. training data on the batched CPM
+    tm = {}
+    t0 = time.perf_counter()
+    X = cw.sweep_points(N, seed0)
+    Y = em.simulate(X, np.arange(N) + 10 ** 6 * seed0, chunk=8192, timings=tm, **sim)
+    data_s = time.perf_counter() - t0
+    t_run_batched = data_s / N
+    # 2. training
+    emu = em.Emulator(init_seed=seed0, max_rows=16384)
+    hist = emu.fit(X, Y, seed=seed0)
+    # 3. error against the CPM at held-out points (truth = mean of R_truth replicates)
+    Q, R = args.emu_eval, 64
+    Xq = cw.sweep_points(Q, seed0 + 99)
+    Yr = em.simulate(np.repeat(Xq, R, axis=0), np.arange(Q * R) + 5 * 10 ** 6 * seed0, chunk=8192, **sim)
+    Yr = Yr.reshape(Q, R, -1)
+    truth = np.nanmean(Yr, axis=1)
+    den = np.nanmean(np.abs(truth), axis=0)
+    loo = (np.nansum(Yr, axis=1, keepdims=True) - Yr) / (R - 1)
+    e1 = np.nanmean(np.abs(Yr - loo), axis=(0, 1)) / den
+    reps = np.ceil((e1 / 0.05) ** 2).astype(int)
+    Yh, _, fb = emu.predict(Xq)
+    emu_err = np.nanmean(np.abs(Yh - truth), axis=0) / den
+    meets = emu_err <= 0.05
+    r_star = int(max(1, reps[meets].max())) if meets.any() else int(reps.max())
+    # 4. timed sweeps: blocks of fresh query points, answered end to end (host in, host out)
+    block = args.emu_block
+    lib_l0 = emu.net.launches()
+    times, n_fb, pts = [], 0, 0
+    for k in range(args.warmup + args.steps):
+        Xs = cw.sweep_points(block, seed0 + 1000 + k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Ys, f = emu.sweep(Xs, seed=seed0 + 2000 + k, replicates=r_star, **sim)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+            n_fb += int(f.sum())
+            pts += block
+    sweep_s = sum(times)
+    t_max = max_over_ranks(dist, sweep_s)
+    value = sum_over_ranks(dist, float(pts)) / t_max
+    launches = emu.net.launches() - lib_l0
+    # 5. inference throughput on 1M device-resident points (the emulator's dominant kernels)
+    Xi = torch.from_numpy(emu._x(cw.sweep_points(1 << 20, seed0 + 3))).cuda()
+    mean = torch.empty((Xi.shape[0], 16), dtype=torch.float32, device="cuda")
+    sd = torch.empty_like(mean)
+    fbi = torch.empty(Xi.shape[0], dtype=torch.uint8, device="cuda")
+    lib = cpm.load()
+    import ctypes
+    for _ in range(2):
+        lib.cpm_mlp_predict(emu.net.h, ctypes.c_void_p(Xi.data_ptr()), Xi.shape[0], ctypes.c_void_p(mean.data_ptr()),
+                            ctypes.c_void_p(sd.data_ptr()), ctypes.c_void_p(fbi.data_ptr()))
+    e0, e1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(5):
+        lib.cpm_mlp_predict(emu.net.h, ctypes.c_void_p(Xi.data_ptr()), Xi.shape[0], ctypes.c_void_p(mean.data_ptr()),
+                            ctypes.c_void_p(sd.data_ptr()), ctypes.c_void_p(fbi.data_ptr()))
+    e1_.record()
+    torch.cuda.synchronize()
+    inf_s = e0.elapsed_time(e1_) / 1e3 / 5
+    sizes = emu.sizes
+    flop_pt = 2.0 * emu.net.n_members * sum(a * b for a, b in zip(sizes[:-1], sizes[1:]))
+    tflops = flop_pt * Xi.shape[0] / inf_s / 1e12
+    # 6. the CPM alone, one lattice at a time (a batch of one: same kernels, one lattice per launch)
+    t0 = time.perf_counter()
+    n_single = 4
+    for i in range(n_single):
+        em.simulate(Xq[i:i + 1], [7 * 10 ** 6 + i], chunk=1, **sim)
+    torch.cuda.synchronize()
+    t_run_single = (time.perf_counter() - t0) / n_single
+    pk = peaks_bf16()
+    if rank == 0:
+        line = {
+            "metric": SWEEP_METRIC, "value": value, "unit": "points/s", "n_gpus": ws_, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16/fp32 (network), int32 (CPM)",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "description": EMULATOR[args.workload],
+                       "training_runs": N, "query_block": block, "eval_points": Q, "truth_replicates": R,
+                       "parallelism": "replicas" if ws_ > 1 else "1 GPU"},
+            "sweep": {
+                "statistics_at_5pct": [em.STATS[k] for k in range(16) if meets[k]],
+                "replicates_for_5pct": int(r_star),
+                "emulator_error": {em.STATS[k]: round(float(emu_err[k]), 4) for k in range(16)},
+                "single_run_cpm_error": {em.STATS[k]: round(float(e1[k]), 4) for k in range(16)},
+                "fallback_fraction": n_fb / max(1, pts),
+                "fallback_fraction_eval": float(fb.mean()),
+                "cpm_batched_points_per_s": 1.0 / (r_star * t_run_batched),
+                "cpm_single_lattice_points_per_s": 1.0 / (r_star * t_run_single),
+                "gain_vs_single_lattice": value / (1.0 / (r_star * t_run_single)),
+                "gain_vs_batched": value / (1.0 / (r_star * t_run_batched)),
+                "cpm_run_s": {"batched": t_run_batched, "single_lattice": t_run_single},
+                "data_s": data_s, "data_cpm_attempts_per_s": tm["attempts"] / tm["cpm"],
+                "train_s": hist["train_s"], "best_epoch": hist["best_epoch"],
+                "val_rmse_std_units": [round(float(v), 4) for v in hist["val_rmse"]],
+            },
+            "roofline": {"bound": "tensor", "achieved": tflops, "peak": pk[0], "unit": "TFLOP/s",
+                         "frac": tflops / pk[0], "traffic": None, "peak_kind": "of %s" % pk[1],
+                         "kernel": "gemm_kernel (emulator inference, 1M points, mma.sync bf16)",
+                         "inference_points_per_s": Xi.shape[0] / inf_s},
+            "cpu_baseline": None,
+            "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": block * 7 * 4,
+                    "d2h_bytes_per_step": block * 16 * 4,
+                    "note": "every step is end to end: parameters in from the host, statistics out to the host"},
+            "gpu_launches": int(launches),
+        }
+        print(json.dumps(line))
+    emu.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + sorted(ENSEMBLES))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    choices=sorted(WORKLOADS) + sorted(ENSEMBLES) + sorted(EMULATOR))
+    ap.add_argument("--emu-runs", type=int, default=100000, help="training runs of the emulator")
+    ap.add_argument("--emu-eval", type=int, default=256, help="held-out points with replicate truth")
+    ap.add_argument("--emu-block", type=int, default=4096, help="query points per sweep step")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -511,6 +703,8 @@ def main():
         return run_reference(args)
     if args.workload in ENSEMBLES:
         return run_gpu_batch(args)
+    if args.workload in EMULATOR:
+        return run_emulator_sweep(args)
     return run_gpu(args)
 
 

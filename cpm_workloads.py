@@ -406,3 +406,79 @@ def ensemble(n: int = 512, seed: int = 1, dim: Optional[int] = None, side2=(64, 
                             lp, at, la, ma, float(hc["T"][k] * S), S, a, c, P, seed * 100003 + k, 2, lat, ct,
                             None, 1000))
     return out
+
+
+# --------------------------------------------------------------------------
+# config 5: inputs of the emulator (swept parameters, network initialisation)
+# --------------------------------------------------------------------------
+
+EMULATOR_PARAMS = list(SWEEP_RANGES)      # input order of the emulator
+EMULATOR_SIDE = 64                         # 2D lattice edge of every emulator run
+EMULATOR_CELLS = 16                        # cells per run (V_t = half the lattice per cell = 128)
+
+
+def sweep_points(n: int, seed: int) -> np.ndarray:
+    """n parameter points [n, 7] (model units, EMULATOR_PARAMS order) from a
+    seeded Latin hypercube over SWEEP_RANGES, rounded to the integer grid
+    the CPM simulates (energies x SWEEP_SCALE, Max_Act to whole MCS)."""
+    hc = latin_hypercube(n, np.random.default_rng(seed))
+    X = np.stack([hc[k] for k in EMULATOR_PARAMS], axis=1)
+    S = SWEEP_SCALE
+    X = np.round(X * S) / S
+    X[:, EMULATOR_PARAMS.index("max_act")] = np.round(X[:, EMULATOR_PARAMS.index("max_act")])
+    return X
+
+
+def scale_inputs(X) -> np.ndarray:
+    """Min-max scaling of parameter points to [0, 1] over SWEEP_RANGES."""
+    lo = np.array([SWEEP_RANGES[k][0] for k in EMULATOR_PARAMS])
+    hi = np.array([SWEEP_RANGES[k][1] for k in EMULATOR_PARAMS])
+    return ((np.asarray(X, dtype=np.float64) - lo) / (hi - lo)).astype(np.float32)
+
+
+def emulator_run(theta, seed: int, side: int = EMULATOR_SIDE, n_cells: int = EMULATOR_CELLS, a: int = 4,
+                 c: int = 2) -> Workload:
+    """One run of the emulator's training set: a 2D side x side periodic
+    lattice, Moore neighbourhood, n_cells cells started as 3 x 3 squares at
+    jittered-grid centres (the config-4 recipe at fixed size and cell count),
+    parameters theta (model units, EMULATOR_PARAMS order), S = SWEEP_SCALE,
+    the checkerboard of config 4 (a x a areas, c x c colours, one round per
+    colour visit).  The seed fixes the start and the Philox key."""
+    rng = np.random.default_rng(seed)
+    th = dict(zip(EMULATOR_PARAMS, np.asarray(theta, dtype=np.float64)))
+    shape = (side, side)
+    spacing = (side * side / n_cells) ** 0.5
+    lat = np.zeros(shape, dtype=np.int32)
+    ctr = jittered_centres(shape, spacing, max(0.0, spacing / 2 - 2), rng)
+    ctr = ctr[rng.permutation(len(ctr))][:n_cells]
+    ncell = place_cubes(lat, ctr, 3)
+    S = SWEEP_SCALE
+    J, lv, vt, lp, at, la, ma = _params()
+    _sym(J, 1, 1, int(round(th["J_cc"] * S)))
+    _sym(J, 1, 0, int(round(th["J_cm"] * S)))
+    lv[1] = int(round(th["lambda_V"] * S))
+    v_t = max(10, int(0.5 * side * side / max(ncell, 1)))
+    vt[1] = v_t
+    lp[1] = int(round(th["lambda_P"] * S))
+    at[1] = int(round(1.2 * 12.5 * v_t ** 0.5))
+    la[1] = int(round(th["lambda_act"] * S))
+    ma[1] = int(round(th["max_act"]))
+    ct = np.ones(ncell + 1, dtype=np.uint8)
+    ct[0] = 0
+    return Workload("emulator_%d" % seed, 2, side, side, 1, J, lv, vt, lp, at, la, ma, float(th["T"] * S), S, a, c,
+                    (a // c) ** 2, seed, 2, lat[None], ct, None, 1)
+
+
+def mlp_init(seed: int, n_members: int, sizes) -> np.ndarray:
+    """Initial parameters of an MLP ensemble, flat float32 [n_members, P] in
+    the layout W_1 [out][in], b_1, W_2, b_2, ...: weights N(0, 2/fan_in)
+    (He et al. 2015), biases zero; each member from its own stream."""
+    out = []
+    for e in range(n_members):
+        rng = np.random.default_rng([seed, e])
+        parts = []
+        for i, o in zip(sizes[:-1], sizes[1:]):
+            parts.append(rng.normal(0.0, (2.0 / i) ** 0.5, (o, i)).ravel())
+            parts.append(np.zeros(o))
+        out.append(np.concatenate(parts))
+    return np.asarray(out, dtype=np.float32)

@@ -222,6 +222,51 @@ int cpm_batch_read_tallies(cpm_batch *b, int32_t idx, int32_t *V, int32_t *A, in
 int cpm_batch_read_act(cpm_batch *b, int32_t idx, uint8_t *dst, int dst_is_device);
 int cpm_batch_stats(cpm_batch *b, int32_t idx, cpm_stats_t *out);
 
+/* Observations of every lattice of b in its current state, for summary
+ * statistics (asynchronous on the batch's stream; call between steps).
+ * cells_out: DEVICE int64 array of rows of 12, one row per cell id 0..n_cells
+ * of each lattice, lattice k's rows starting at sum_{j<k} (n_cells_j + 1);
+ * row 0 of a lattice (the medium) is unused.  Per cell:
+ *   [0] anchor: linear index z*ny*nx + y*nx + x of the cell's first site in
+ *       raster order, -1 when the cell has no site;
+ *   [1] volume (sites);
+ *   [2..4] sums over the cell's sites of the minimal-image offsets
+ *       ((p - anchor + n/2) mod n) - n/2 from the anchor along x, y, z, so the
+ *       centroid (Methods, "Composite variable tracking", Eq. 10) is
+ *       anchor + sums / volume, modulo the lattice, for any cell shorter than
+ *       half the lattice along each axis;
+ *   [5] interface count: neighbour pairs with a different id (Eq. 3);
+ *   [6..11] sums of the offset products xx, yy, zz, xy, xz, yz (the cell's
+ *       second moments about the anchor; z terms are 0 in 2D).
+ * member_out: DEVICE int64 [n][2]: unordered (cell, medium) neighbour pairs
+ * over the model's neighbourhood, and accepted copies since creation.
+ * Three kernel launches; the first call uploads one descriptor per lattice. */
+int cpm_batch_observe(cpm_batch *b, int64_t *cells_out, int64_t *member_out);
+
+/* Summary statistics of every lattice of a 2D batch from n_snap
+ * observations taken every `every` MCS (cpm_batch_observe outputs stacked
+ * on the device: cells_hist [n_snap][rows][12], member_hist [n_snap][n][2]).
+ * out: DEVICE double [n][16], NaN where a statistic is undefined:
+ *   0 mean cell volume / V_t, 1 std of the volume over cells / V_t (root
+ *   of the per-snapshot variance averaged over snapshots), 2 mean interface
+ *   count / A_t, 3 its std / A_t (V_t, A_t of cell 1's type);
+ *   4..6 mean squared centroid displacement over 10, 50 and 200 MCS;
+ *   7, 8 mean and std of the centroid speed over `every`-MCS steps;
+ *   9 mean cosine between successive 50-MCS displacements;
+ *   10 persistence time: every * (1/2 + sum of the step-direction
+ *      autocorrelation over lags 1..20 up to its first value <= 0);
+ *   11 arrest coefficient: share of 50-MCS sub-tracks slower than 0.05
+ *      sites / MCS;
+ *   12 acceptance rate over the window; 13 cell-cell share of the cells'
+ *      interface pairs; 14 net displacement / path length;
+ *   15 elongation: sqrt of the ratio of the principal second moments.
+ * Centroids follow Methods, "Composite variable tracking" (Eq. 10); a cell
+ * absent at some snapshot counts for 0..3, 13 and 15 only.  One kernel
+ * launch; the batch keeps a scratch track buffer of n_snap * 2 * rows
+ * doubles.  Asynchronous on the batch's stream. */
+int cpm_batch_summarize(cpm_batch *b, const int64_t *cells_hist, const int64_t *member_hist, int32_t n_snap,
+                        int32_t every, double *out);
+
 /* Kernel launches issued for b (set-up included). */
 int64_t cpm_batch_kernel_launches(const cpm_batch *b);
 

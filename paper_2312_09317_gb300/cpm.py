@@ -18,6 +18,7 @@ from . import build as _build
 MAX_TYPES = 8
 
 CPM_OK, CPM_E_INVALID, CPM_E_NOMEM, CPM_E_CUDA, CPM_E_HANDLE, CPM_E_STATE, CPM_E_LIMIT = 0, -1, -2, -3, -4, -5, -6
+OBS_FIELDS = 12  # per-cell fields of cpm_batch_observe
 
 
 class Config(ctypes.Structure):
@@ -81,10 +82,39 @@ _SIGNATURES = {
     "cpm_batch_kernel_launches": (ctypes.c_int64, [ctypes.c_void_p]),
     "cpm_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "cpm_batch_destroy": (None, [ctypes.c_void_p]),
+    "cpm_batch_observe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "cpm_batch_summarize": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.c_void_p]),
     "cpm_step_noalloc": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64,
                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
 }
+
+
+class MlpShape(ctypes.Structure):
+    """cpm_mlp_shape (include/cpm_emulator.h)."""
+    _fields_ = [("n_members", ctypes.c_int32), ("n_in", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("n_hidden", ctypes.c_int32), ("n_out", ctypes.c_int32), ("max_rows", ctypes.c_int32)]
+
+
+_VP, _I64, _I32, _F = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float
+_SIGNATURES.update({
+    "cpm_mlp_param_count": (_I64, [ctypes.POINTER(MlpShape)]),
+    "cpm_mlp_create": (ctypes.c_int, [ctypes.POINTER(MlpShape), _VP, _VP, ctypes.POINTER(_VP)]),
+    "cpm_mlp_set_params": (ctypes.c_int, [_VP, _VP]),
+    "cpm_mlp_get_params": (ctypes.c_int, [_VP, _VP]),
+    "cpm_mlp_grads": (ctypes.c_int, [_VP, _VP, _VP, _I64, _VP, _I64, _I32, _VP, _VP]),
+    "cpm_mlp_train": (ctypes.c_int, [_VP, _VP, _VP, _I64, _VP, _I64, _I32, _F, _F, _F, _F, _VP]),
+    "cpm_mlp_forward": (ctypes.c_int, [_VP, _VP, _I64, _VP]),
+    "cpm_mlp_set_output_transform": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _F]),
+    "cpm_mlp_predict": (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP, _VP]),
+    "cpm_mlp_kernel_launches": (ctypes.c_uint64, [_VP]),
+    "cpm_mlp_last_error": (ctypes.c_char_p, [_VP]),
+    "cpm_mlp_destroy": (ctypes.c_int, [_VP]),
+    "cpm_mlp_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    _VP, _I64, _I64, _VP, _I64, _I64, _VP, _I64, _VP, ctypes.c_int, _I64, _I64,
+                                    _VP, _I64, _I64, ctypes.c_int, _VP]),
+})
 
 _lib = None
 
@@ -300,6 +330,30 @@ class Batch:
         s = Stats()
         self._check(self.lib.cpm_batch_stats(self.b, idx, ctypes.byref(s)))
         return s.as_dict()
+
+    def observation_rows(self) -> np.ndarray:
+        """First observation row of every lattice (its medium row) and, last, the total."""
+        return np.concatenate([[0], np.cumsum([w.n_cells + 1 for w in self.ws])]).astype(np.int64)
+
+    def observe(self, cells_out, member_out):
+        """cpm_batch_observe into device int64 tensors cells_out [rows, 12] and
+        member_out [n, 2] (asynchronous on the batch's stream)."""
+        pc, dc = _ptr(cells_out)
+        pm, dm = _ptr(member_out)
+        if not (dc and dm):
+            raise ValueError("observe writes device buffers")
+        self._check(self.lib.cpm_batch_observe(self.b, ctypes.c_void_p(pc), ctypes.c_void_p(pm)))
+
+    def summarize(self, cells_hist, member_hist, every: int, out):
+        """cpm_batch_summarize: device tensors cells_hist [S, rows, 12],
+        member_hist [S, n, 2] -> out [n, 16] float64 (asynchronous)."""
+        pc, dc = _ptr(cells_hist)
+        pm, dm = _ptr(member_hist)
+        po, do = _ptr(out)
+        if not (dc and dm and do):
+            raise ValueError("summarize works on device buffers")
+        self._check(self.lib.cpm_batch_summarize(self.b, ctypes.c_void_p(pc), ctypes.c_void_p(pm),
+                                                 int(cells_hist.shape[0]), every, ctypes.c_void_p(po)))
 
     def launches(self) -> int:
         return int(self.lib.cpm_batch_kernel_launches(self.b))

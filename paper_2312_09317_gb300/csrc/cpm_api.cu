@@ -5,7 +5,9 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <new>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -39,6 +41,8 @@ struct cpm_handle {
     // tiled schedule
     uint32_t tile = 0, tile_cycles = 1, CT = 1;
     int *error_flag = nullptr;
+    bool shared_tables = false;  // thr / ln_tab / expq belong to a batch's table cache
+    double v_ref = 0.0, a_ref = 0.0;  // V_t, A_t of cell 1's type (scales of the summary statistics)
     // position
     int64_t t = 0;
     int32_t sp = 0;
@@ -334,24 +338,96 @@ int check_error_flag(cpm_handle *h)
     return CPM_OK;
 }
 
-int build_tables(cpm_handle *h)
+// THR[h] = min(2^32-1, floor(2^32 exp(-h/(16T)))) up to the first zero; false when longer than 2^22
+bool thr_table(double T, std::vector<uint32_t> &thr)
 {
-    // THR[h] = min(2^32-1, floor(2^32 exp(-h/(16T)))) up to the first zero
-    std::vector<uint32_t> thr;
-    const double T = h->cfg.temperature;
+    thr.clear();
     for (int64_t e = 0;; e++) {
         const double v = std::floor(std::ldexp(std::exp(-(double)e / (16.0 * T)), 32));
         if (v <= 0.0) break;
         thr.push_back(v >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)v);
-        if (thr.size() > (1u << 22)) return fail(h, CPM_E_INVALID, "threshold table too long");
+        if (thr.size() > (1u << 22)) return false;
     }
-    h->L = (int32_t)thr.size();
-    // LN[a] = round(2^16 ln a), EXPQ[m] = round(2^16 exp(m/1024))
-    std::vector<int32_t> ln(kLnEntries, 0);
+    return true;
+}
+
+// LN[a] = round(2^16 ln a), EXPQ[m] = round(2^16 exp(m/1024))
+void ln_expq_tables(std::vector<int32_t> &ln, std::vector<int32_t> &ex)
+{
+    ln.assign(kLnEntries, 0);
     for (int a = 1; a < kLnEntries; a++) ln[a] = (int32_t)std::llround(std::ldexp(std::log((double)a), 16));
     const int32_t ne = (ln[kLnEntries - 1] >> 6) + 1;
-    std::vector<int32_t> ex(ne);
+    ex.resize(ne);
     for (int m = 0; m < ne; m++) ex[m] = (int32_t)std::llround(std::ldexp(std::exp((double)m / 1024.0), 16));
+}
+
+}  // namespace
+
+// Tables shared by the lattices of a batch: LN / EXPQ once, THR once per
+// temperature (keyed by the bit pattern of T).
+struct TableCache {
+    std::map<uint64_t, std::pair<uint32_t *, int32_t>> thr;
+    std::map<uint64_t, std::vector<uint32_t>> host_thr;  // precomputed, not yet uploaded
+    int32_t *ln = nullptr, *expq = nullptr;
+    std::vector<void *> owned;
+    ~TableCache()
+    {
+        for (void *p : owned) cudaFree(p);
+    }
+};
+
+namespace {
+
+uint64_t t_key(double T)
+{
+    uint64_t k;
+    memcpy(&k, &T, sizeof k);
+    return k;
+}
+
+int build_tables_cached(cpm_handle *h, TableCache *cache)
+{
+    if (!cache->ln) {
+        std::vector<int32_t> ln, ex;
+        ln_expq_tables(ln, ex);
+        CUDA_TRY(h, cudaMalloc(&cache->ln, sizeof(int32_t) * ln.size()));
+        cache->owned.push_back(cache->ln);
+        CUDA_TRY(h, cudaMalloc(&cache->expq, sizeof(int32_t) * ex.size()));
+        cache->owned.push_back(cache->expq);
+        CUDA_TRY(h, cudaMemcpy(cache->ln, ln.data(), sizeof(int32_t) * ln.size(), cudaMemcpyHostToDevice));
+        CUDA_TRY(h, cudaMemcpy(cache->expq, ex.data(), sizeof(int32_t) * ex.size(), cudaMemcpyHostToDevice));
+    }
+    const uint64_t key = t_key(h->cfg.temperature);
+    auto it = cache->thr.find(key);
+    if (it == cache->thr.end()) {
+        std::vector<uint32_t> local;
+        auto pre = cache->host_thr.find(key);
+        std::vector<uint32_t> &thr = pre != cache->host_thr.end() ? pre->second : local;
+        if (pre == cache->host_thr.end() || thr.empty()) {
+            if (!thr_table(h->cfg.temperature, thr)) return fail(h, CPM_E_INVALID, "threshold table too long");
+        }
+        uint32_t *d = nullptr;
+        CUDA_TRY(h, cudaMalloc(&d, sizeof(uint32_t) * thr.size()));
+        cache->owned.push_back(d);
+        CUDA_TRY(h, cudaMemcpy(d, thr.data(), sizeof(uint32_t) * thr.size(), cudaMemcpyHostToDevice));
+        it = cache->thr.emplace(key, std::make_pair(d, (int32_t)thr.size())).first;
+        if (pre != cache->host_thr.end()) cache->host_thr.erase(pre);
+    }
+    h->thr = it->second.first;
+    h->L = it->second.second;
+    h->ln_tab = cache->ln;
+    h->expq = cache->expq;
+    h->shared_tables = true;
+    return CPM_OK;
+}
+
+int build_tables(cpm_handle *h)
+{
+    std::vector<uint32_t> thr;
+    if (!thr_table(h->cfg.temperature, thr)) return fail(h, CPM_E_INVALID, "threshold table too long");
+    h->L = (int32_t)thr.size();
+    std::vector<int32_t> ln, ex;
+    ln_expq_tables(ln, ex);
     CUDA_TRY(h, cudaMalloc(&h->thr, sizeof(uint32_t) * thr.size()));
     CUDA_TRY(h, cudaMalloc(&h->ln_tab, sizeof(int32_t) * ln.size()));
     CUDA_TRY(h, cudaMalloc(&h->expq, sizeof(int32_t) * ex.size()));
@@ -369,15 +445,17 @@ void free_all(cpm_handle *h)
     cudaFree(h->cell_type);
     cudaFree(h->tallies);
     cudaFree(h->pend);
-    cudaFree(h->thr);
-    cudaFree(h->ln_tab);
-    cudaFree(h->expq);
+    if (!h->shared_tables) {
+        cudaFree(h->thr);
+        cudaFree(h->ln_tab);
+        cudaFree(h->expq);
+    }
     cudaFree(h->counters);
     cudaFree(h->act_tmp);
     cudaFree(h->error_flag);
 }
 
-int create_impl(cpm_handle *h, const cpm_config *c)
+int create_impl(cpm_handle *h, const cpm_config *c, TableCache *cache = nullptr)
 {
     h->cfg = *c;
     h->cfg.cell_type = nullptr;
@@ -416,6 +494,10 @@ int create_impl(cpm_handle *h, const cpm_config *c)
     h->t = c->t0;
     h->sp = 0;
     h->g = 0;
+    if (c->n_cells >= 1) {
+        h->v_ref = c->v_target[c->cell_type[1]];
+        h->a_ref = c->a_target[c->cell_type[1]];
+    }
 
     const size_t nv = (size_t)h->n_cells + 1;
     CUDA_TRY(h, cudaMalloc(&h->lat, sizeof(int32_t) * h->n_sites));
@@ -443,14 +525,34 @@ int create_impl(cpm_handle *h, const cpm_config *c)
                 st[x] = (uint8_t)((c->t0 - 128) & 255);
         }
         CUDA_TRY(h, cudaMalloc(&h->stamp, h->n_sites));
+        // a copy from pageable memory returns once the source has been staged
         CUDA_TRY(h, cudaMemcpyAsync(h->stamp, st.data(), h->n_sites, cudaMemcpyHostToDevice, h->stream));
-        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     }
-    int rc = build_tables(h);
+    int rc = cache ? build_tables_cached(h, cache) : build_tables(h);
     if (rc) return rc;
     rc = reset_tallies(h);
     if (rc) return rc;
-    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (!cache) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return CPM_OK;
+}
+
+// cpm_create for a member of a batch: tables from the batch's cache, no stream synchronisation
+int create_member(const cpm_config *cfg, void *cuda_stream, TableCache *cache, cpm_handle **out)
+{
+    *out = nullptr;
+    int rc = validate(cfg);
+    if (rc) return rc;
+    cpm_handle *h = new (std::nothrow) cpm_handle();
+    if (!h) return fail(nullptr, CPM_E_NOMEM, "host allocation failed");
+    h->stream = (cudaStream_t)cuda_stream;
+    rc = create_impl(h, cfg, cache);
+    if (rc) {
+        g_create_error = h->err;
+        free_all(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
     return CPM_OK;
 }
 
@@ -640,6 +742,13 @@ struct cpm_batch {
     BatchLattice *d_lats = nullptr;
     int2 *d_items = nullptr;
     int2 *d_clamp = nullptr;
+    ObserveItem *d_obs = nullptr;        // observation items, built on first use
+    TableCache *tables = nullptr;        // LN / EXPQ / THR shared by the members
+    int64_t obs_max_sites = 0;
+    int64_t obs_rows = 0;
+    int32_t obs_max_cells = 0;
+    double *traj = nullptr;              // centroid tracks of cpm_batch_summarize
+    size_t traj_cap = 0;
     cudaGraphExec_t graph = nullptr;     // one MCS of every member
     int64_t graph_launches = 0;          // kernels in one replay
     bool descriptors_dirty = true;
@@ -666,9 +775,13 @@ void batch_free(cpm_batch *b)
 {
     batch_drop_graph(b);
     for (cpm_handle *h : b->hs) cpm_destroy(h);
+    delete b->tables;
+    b->tables = nullptr;
     cudaFree(b->d_lats);
     cudaFree(b->d_items);
     cudaFree(b->d_clamp);
+    cudaFree(b->d_obs);
+    cudaFree(b->traj);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
 }
 
@@ -767,6 +880,33 @@ int cpm_batch_create(const cpm_config *cfgs, int32_t n, void *cuda_stream, cpm_b
     b->stream = (cudaStream_t)cuda_stream;
     b->dim = cfgs[0].dim;
     if (b->dim == 2) { b->brick[0] = 16; b->brick[1] = 8; b->brick[2] = 1; }
+    b->tables = new (std::nothrow) TableCache();
+    if (!b->tables) {
+        delete b;
+        return bfail(nullptr, CPM_E_NOMEM, "host allocation failed");
+    }
+    {
+        // the threshold tables of the distinct temperatures, computed on host threads
+        std::vector<double> temps;
+        for (int32_t i = 0; i < n; i++) {
+            const double T = cfgs[i].temperature;
+            if (T > 0.0 && T <= 1e4 && !b->tables->host_thr.count(t_key(T))) {
+                b->tables->host_thr[t_key(T)];
+                temps.push_back(T);
+            }
+        }
+        std::vector<std::vector<uint32_t> *> slots;
+        for (double T : temps) slots.push_back(&b->tables->host_thr[t_key(T)]);
+        const unsigned hw = std::thread::hardware_concurrency();
+        const size_t nt = std::min<size_t>(temps.size(), std::max(1u, std::min(hw, 16u)));
+        std::vector<std::thread> pool;
+        for (size_t w = 0; w < nt; w++)
+            pool.emplace_back([&, w]() {
+                for (size_t j = w; j < temps.size(); j += nt)
+                    if (!thr_table(temps[j], *slots[j])) slots[j]->clear();
+            });
+        for (auto &th : pool) th.join();
+    }
     for (int32_t i = 0; i < n; i++) {
         if (cfgs[i].dim != b->dim || cfgs[i].tile != 0) {
             batch_free(b);
@@ -774,7 +914,7 @@ int cpm_batch_create(const cpm_config *cfgs, int32_t n, void *cuda_stream, cpm_b
             return bfail(nullptr, CPM_E_INVALID, "a batch needs one dimension and the global schedule (tile = 0)");
         }
         cpm_handle *h = nullptr;
-        int rc = cpm_create(&cfgs[i], cuda_stream, &h);
+        int rc = create_member(&cfgs[i], cuda_stream, b->tables, &h);
         if (rc) {
             std::string msg = "configuration " + std::to_string(i) + ": " + cpm_last_error(nullptr);
             batch_free(b);
@@ -832,6 +972,12 @@ int cpm_batch_create(const cpm_config *cfgs, int32_t n, void *cuda_stream, cpm_b
         batch_free(b);
         delete b;
         return bfail(nullptr, rc, msg);
+    }
+    e = cudaStreamSynchronize(b->stream);  // the members' uploads and tally counts
+    if (e != cudaSuccess) {
+        batch_free(b);
+        delete b;
+        return bfail(nullptr, CPM_E_CUDA, cudaGetErrorString(e));
     }
     *out = b;
     return CPM_OK;
@@ -974,6 +1120,84 @@ int64_t cpm_batch_kernel_launches(const cpm_batch *b)
 }
 
 const char *cpm_batch_last_error(const cpm_batch *b) { return b ? b->err.c_str() : g_batch_create_error.c_str(); }
+
+namespace {
+int batch_obs_items(cpm_batch *b)
+{
+    if (!b->d_obs) {
+        std::vector<ObserveItem> items(b->hs.size());
+        int64_t row = 0;
+        for (size_t l = 0; l < b->hs.size(); l++) {
+            const cpm_handle *h = b->hs[l];
+            ObserveItem &it = items[l];
+            it.lat = h->lat;
+            it.accepts = h->counters;
+            it.nx = (uint32_t)h->cfg.nx;
+            it.ny = (uint32_t)h->cfg.ny;
+            it.nz = (uint32_t)(h->dim == 3 ? h->cfg.nz : 1);
+            it.dim = (uint32_t)h->dim;
+            it.row0 = row;
+            it.n_cells = h->n_cells;
+            it.pad_ = 0;
+            it.v_ref = h->v_ref;
+            it.a_ref = h->a_ref;
+            row += (int64_t)h->n_cells + 1;
+            b->obs_max_sites = std::max<int64_t>(b->obs_max_sites, (int64_t)h->n_sites);
+            b->obs_max_cells = std::max<int32_t>(b->obs_max_cells, h->n_cells);
+        }
+        b->obs_rows = row;
+        cudaError_t e = cudaMalloc(&b->d_obs, sizeof(ObserveItem) * items.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_obs, items.data(), sizeof(ObserveItem) * items.size(), cudaMemcpyHostToDevice,
+                                b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) {
+            cudaFree(b->d_obs);
+    cudaFree(b->traj);
+            b->d_obs = nullptr;
+            return bfail(b, CPM_E_CUDA, cudaGetErrorString(e));
+        }
+    }
+    return CPM_OK;
+}
+}  // namespace
+
+int cpm_batch_observe(cpm_batch *b, int64_t *cells_out, int64_t *member_out)
+{
+    if (!b) return CPM_E_HANDLE;
+    if (!cells_out || !member_out) return bfail(b, CPM_E_INVALID, "cells_out and member_out are required");
+    if (int rc = batch_obs_items(b)) return rc;
+    cudaError_t e = launch_observe(b->dim, b->d_obs, (uint32_t)b->hs.size(), b->obs_max_sites, cells_out, member_out,
+                                   b->stream);
+    if (e != cudaSuccess) return bfail(b, CPM_E_CUDA, cudaGetErrorString(e));
+    b->launches += 3;
+    return CPM_OK;
+}
+
+int cpm_batch_summarize(cpm_batch *b, const int64_t *cells_hist, const int64_t *member_hist, int32_t n_snap,
+                        int32_t every, double *out)
+{
+    if (!b) return CPM_E_HANDLE;
+    if (!cells_hist || !member_hist || !out) return bfail(b, CPM_E_INVALID, "null buffer");
+    if (b->dim != 2) return bfail(b, CPM_E_INVALID, "summary statistics are defined for 2D lattices");
+    if (n_snap < 1 || n_snap > kSummaryMaxSnap) return bfail(b, CPM_E_INVALID, "n_snap must be in 1..1024");
+    if (every < 1) return bfail(b, CPM_E_INVALID, "every must be >= 1");
+    if (int rc = batch_obs_items(b)) return rc;
+    const size_t need = (size_t)b->obs_rows * 2 * (size_t)n_snap;
+    if (need > b->traj_cap) {
+        cudaFree(b->traj);
+        b->traj = nullptr;
+        b->traj_cap = 0;
+        cudaError_t e = cudaMalloc(&b->traj, sizeof(double) * need);
+        if (e != cudaSuccess) return bfail(b, CPM_E_NOMEM, cudaGetErrorString(e));
+        b->traj_cap = need;
+    }
+    cudaError_t e = launch_summarize(b->d_obs, (uint32_t)b->hs.size(), b->obs_max_cells, cells_hist, b->obs_rows,
+                                     member_hist, n_snap, every, b->traj, out, b->stream);
+    if (e != cudaSuccess) return bfail(b, CPM_E_CUDA, cudaGetErrorString(e));
+    b->launches += 1;
+    return CPM_OK;
+}
 
 void cpm_batch_destroy(cpm_batch *b)
 {

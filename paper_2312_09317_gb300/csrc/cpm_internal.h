@@ -109,6 +109,26 @@ cudaError_t launch_batch_round(int dim, bool perim, bool act, const BatchLattice
 cudaError_t launch_batch_clamp(const BatchLattice *lats, const int2 *items, uint32_t n_items, cudaStream_t st);
 cudaError_t launch_batch_advance(BatchLattice *lats, uint32_t n, cudaStream_t st);
 
+// Observations of a batch (cpm_batch_observe): one item per lattice.
+constexpr int kObsFields = 12;  // anchor, volume, offset sums x y z, interface count, xx yy zz xy xz yz
+struct ObserveItem {
+    const int32_t *lat;
+    const unsigned long long *accepts;
+    uint32_t nx, ny, nz, dim;
+    int64_t row0;  // first output row of this lattice (its medium row)
+    int32_t n_cells, pad_;
+    double v_ref, a_ref;  // V_t and A_t of cell 1's type: the scale of the volume / interface statistics
+};
+cudaError_t launch_observe(int dim, const ObserveItem *d_items, uint32_t n_items, int64_t max_sites, int64_t *cells,
+                           int64_t *member, cudaStream_t st);
+
+// Summary statistics of 2D lattices from a stack of observations (cpm_batch_summarize).
+constexpr int kSummaryStats = 16;
+constexpr int kSummaryMaxSnap = 1024;
+cudaError_t launch_summarize(const ObserveItem *d_items, uint32_t n_items, int32_t max_cells, const int64_t *cells,
+                             int64_t rows, const int64_t *member, int32_t n_snap, int32_t every, double *traj,
+                             double *out, cudaStream_t st);
+
 // Tiled schedule: everything one epoch of one tile colour needs.
 constexpr int kMaxEpochSubpasses = 512;
 constexpr uint32_t kTileHashCap = 512;  // distinct ids a tile and its halo may hold (incl. medium, obstacle)

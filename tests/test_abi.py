@@ -1,5 +1,5 @@
 """The C ABI library on a machine without a GPU: it builds, loads, exports every
-function include/cpm.h declares, and rejects invalid configurations before
+function the headers under include/ declare, and rejects invalid configurations before
 touching the device."""
 import ctypes
 import os
@@ -16,9 +16,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared_functions():
-    src = open(os.path.join(ROOT, "include", "cpm.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(cpm_[a-z_]+)\s*\(", src)))
+    names = set()
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(cpm_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")

@@ -166,3 +166,21 @@ def test_interface_tallies_split_into_cell_cell_and_cell_medium():
         cc += int(((g > 0) & (nb > 0) & (nb != g)).sum())
     assert cc % 2 == 0
     assert int(A[1:].sum()) == cc + cm
+
+
+def test_cell_rows_agree_with_brute_tallies_and_a_hand_moment():
+    import cpm_workloads as cw
+    from tests import brute
+    for dim in (2, 3):
+        w = cw.random_small(21 + dim, dim=dim, n=16, n_cells=6, edge=3, obstacles=0.05)
+        rows = observe.cell_rows(w.lattice, w.n_cells, dim)
+        assert list(rows[0]) == [-1] + [0] * 11
+        assert np.array_equal(rows[1:, 1], brute.volumes(w, w.lattice)[1:])
+        assert np.array_equal(rows[1:, 5], brute.interfaces(w, w.lattice)[1:])
+        a, cnt, sums = observe.centroid_sums(w.lattice, w.n_cells)
+        assert np.array_equal(rows[:, 0], a) and np.array_equal(rows[:, 2:5], sums)
+    # a 1 x 3 bar along x with the anchor at its left end: offsets 0, 1, 2
+    lat = np.zeros((1, 8, 8), np.int32)
+    lat[0, 4, 2:5] = 1
+    r = observe.cell_rows(lat, 1, 2)[1]
+    assert list(r[[2, 3, 6, 7, 9]]) == [3, 0, 5, 0, 0]
