@@ -25,6 +25,7 @@ from __future__ import annotations
 import ctypes
 import math
 import time
+import warnings
 
 import numpy as np
 
@@ -203,6 +204,7 @@ def simulate(thetas, seeds, burn=200, window=800, every=10, chunk=2048, stream=N
         b.summarize(cells, member, every, st)
         out[c0:c0 + len(ws)] = st.cpu().numpy()
         t2 = time.perf_counter()
+        tm["launches"] = tm.get("launches", 0) + b.launches()
         b.close()
         t3 = time.perf_counter()
         tm["create"] = tm.get("create", 0.0) + (t1 - t0)
@@ -309,7 +311,9 @@ class Emulator:
             rep_th = np.repeat(np.asarray(thetas)[idx], replicates, axis=0)
             rep_seed = seed * 1000003 + np.arange(rep_th.shape[0])
             Ys = simulate(rep_th, rep_seed, timings=timings, **sim).reshape(idx.size, replicates, -1)
-            Yhat[idx] = np.nanmean(Ys, axis=1)
+            with warnings.catch_warnings():
+                warnings.simplefilter("ignore", RuntimeWarning)  # a statistic undefined in every replicate stays NaN
+                Yhat[idx] = np.nanmean(Ys, axis=1)
         return Yhat, fb
 
     def close(self):
