@@ -95,11 +95,11 @@ DEFAULT_WORKLOAD = "cpm3d_tissue_1024"
 # DRAM bytes per round-kernel launch from the last ncu capture, valid only for
 # the kernel source it was taken on (sha1 of csrc/cpm_kernels.cu, first 12 hex).
 # The 1024^3 tissue launch is too large to capture; its figure is the 512^3
-# capture (503.8 MB read + 65.7 MB written per launch) scaled by the 8x sites:
+# capture (503.8 MB read + 65.2 MB written per launch) scaled by the 8x sites:
 # one round streams the lattice once, so traffic grows with the sites.
 NCU_TRAFFIC = {
-    ("cpm3d_tissue_1024", "1d35e3cef5a6"): 8 * (503.821568e6 + 65.669632e6),
-    ("cpm3d_tissue_512", "1d35e3cef5a6"): 503.821568e6 + 65.669632e6,
+    ("cpm3d_tissue_1024", "d49ef2000078"): 8 * (503.849216e6 + 65.235456e6),
+    ("cpm3d_tissue_512", "d49ef2000078"): 503.849216e6 + 65.235456e6,
 }
 
 
