@@ -577,7 +577,7 @@ def run_emulator_sweep(args):
     data_s = time.perf_counter() - t0
     t_run_batched = data_s / N
     # 2. training
-    emu = em.Emulator(init_seed=seed0, max_rows=16384)
+    emu = em.Emulator(init_seed=seed0, max_rows=65536)
     hist = emu.fit(X, Y, seed=seed0)
     # 3. error against the CPM at held-out points (truth = mean of R_truth replicates)
     Q, R = args.emu_eval, 64

@@ -10,9 +10,11 @@
 // runs all members in one launch (grid.z = member), each member reading its
 // own slice of the flat parameter buffer.
 //
-// GEMMs use the tensor cores through mma.sync m16n8k16 (bf16 x bf16 -> f32)
-// on 64 x 64 CTA tiles with a 32-deep K slab, double-buffered in shared
-// memory; the bias, GELU and GELU' steps are fused into their epilogues.
+// The forward layers (A [M][K] times W^T, N <= 256, K <= 256) run on the
+// fifth-generation tensor cores (tcgen05.mma into TMEM, gemm_tc_kernel).  The
+// backward GEMMs (transposed operands) use mma.sync m16n8k16 (bf16 x bf16 ->
+// f32) on 64 x 64 CTA tiles with a 32-deep K slab, double-buffered in shared
+// memory.  Bias, GELU and GELU' are fused into the epilogues.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -312,6 +314,270 @@ __global__ void predict_kernel(int rows, int n_members, int n_out, const float *
     if (fallback) fallback[r] = (uint8_t)fb;
 }
 
+// ---------------------------------------------------------------------------
+// Forward GEMM on the fifth-generation tensor cores: C = epi(A W^T + b) with
+// A [M][K] and W [N][K] both K-major (the layout of every forward layer).
+// Persistent CTAs take contiguous ranges of 128-row tiles (members outer), so
+// a member's weights are staged once per CTA.  The weight slab (N x Kp) and
+// the activation tile (128 x Kp) sit in shared memory in the canonical
+// no-swizzle K-major layout: 8-row x 16-byte core matrices, K-adjacent core
+// matrices 128 B apart (leading byte offset), 8-row groups Kp/8 x 128 B apart
+// (stride byte offset).  One thread issues Kp/16 tcgen05.mma (bf16 x bf16 ->
+// f32, M = 128, N <= 256) into a TMEM accumulator and commits them to an
+// mbarrier; after a bounded wait the eight warps read the accumulator with
+// tcgen05.ld (warp w owns TMEM lanes 32 (w % 4) .. + 31 and every other
+// 16-column chunk) and apply the bias / GELU epilogue.
+constexpr int kTcThreads = 256;
+constexpr int kTcM = 128;
+constexpr uint32_t kTcSpinLimit = 1u << 22;
+constexpr int kTcNotApplicable = 1;  // launch_gemm_tc: use the mma.sync kernel instead
+
+struct TcArgs {
+    int M, N, K, Kp, ncols;
+    const __nv_bfloat16 *A;
+    int64_t lda, sa;
+    const __nv_bfloat16 *B;
+    int64_t ldb, sb;
+    const float *bias;
+    int64_t sbias;
+    void *C;
+    int64_t ldc, sc;
+    float *Z;
+    int64_t ldz, sz;
+    int epi, c_f32, vec_a, vec_b, vec_c;
+    int mtiles, tiles;
+    int *err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t parity)
+{
+    const uint32_t addr = smem_u32(mbar);
+    for (uint32_t it = 0; it < kTcSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(addr), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// rows [r0, r0 + rows_tile) x [0, Kp) of X into the core-matrix layout, zero outside [0, rows) x [0, K);
+// element e of the layout is core matrix e / 8 (8-row group outer, K chunk inner), row e % 8
+__device__ __forceinline__ void tc_stage(unsigned char *S, const __nv_bfloat16 *X, int64_t ld, int rows, int K, int r0,
+                                         int rows_tile, int Kp, bool vec)
+{
+    const int kc = Kp / 8;
+    const int n = rows_tile * kc;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int rr = e & 7, k8 = (e >> 3) % kc, r8 = (e >> 3) / kc;
+        const int gr = r0 + r8 * 8 + rr, gk = k8 * 8;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (gr < rows) {
+            if (vec && gk + 8 <= K) {
+                v = *reinterpret_cast<const uint4 *>(X + (int64_t)gr * ld + gk);
+            } else {
+                __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) h[j] = gk + j < K ? X[(int64_t)gr * ld + gk + j] : __float2bfloat16(0.0f);
+                v = *reinterpret_cast<const uint4 *>(h);
+            }
+        }
+        *reinterpret_cast<uint4 *>(S + (size_t)e * 16) = v;
+    }
+}
+
+// As tc_stage for 16-byte aligned rows with K a multiple of 8, issued as
+// cp.async copies (rows past `rows` are zero-filled without reading);
+// completion: cp.async.wait_all, then fence.proxy.async before the MMAs read.
+__device__ __forceinline__ void tc_stage_async(unsigned char *S, const __nv_bfloat16 *X, int64_t ld, int rows, int r0,
+                                               int rows_tile, int Kp)
+{
+    const int kc = Kp / 8;
+    const int n = rows_tile * kc;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int rr = e & 7, k8 = (e >> 3) % kc, r8 = (e >> 3) / kc;
+        const int gr = r0 + r8 * 8 + rr;
+        const bool in = gr < rows;
+        const __nv_bfloat16 *src = X + (in ? (int64_t)gr * ld + k8 * 8 : 0);
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(S + (size_t)e * 16);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(in ? 16 : 0)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const TcArgs p)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    unsigned char *Bs = tc_smem;                                          // N x Kp
+    unsigned char *As = tc_smem + (size_t)p.N * p.Kp * 2;                 // 128 x Kp
+    float *bias_s = reinterpret_cast<float *>(tc_smem + (size_t)(p.N + kTcM) * p.Kp * 2);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"((uint32_t)p.ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const int t0 = (int)((int64_t)p.tiles * blockIdx.x / gridDim.x);
+    const int t1 = (int)((int64_t)p.tiles * (blockIdx.x + 1) / gridDim.x);
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(p.N >> 3) << 17) |
+                           ((uint32_t)(kTcM >> 4) << 24);
+    const uint32_t sbo = (uint32_t)(p.Kp / 8) * 128u;
+    const int q = warp & 3, half = warp >> 2, nchunk = p.N / 16;
+    int cur_z = -1;
+    uint32_t phase = 0;
+    bool aborted = false;
+    // the activation tile of the first tile; later tiles are prefetched during the previous epilogue
+    const bool async_a = p.vec_a && p.K % 8 == 0;
+    if (t0 < t1) {
+        const int z = t0 / p.mtiles, m0 = (t0 % p.mtiles) * kTcM;
+        if (async_a) {
+            tc_stage_async(As, p.A + z * p.sa, p.lda, p.M, m0, kTcM, p.Kp);
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+        } else {
+            tc_stage(As, p.A + z * p.sa, p.lda, p.M, p.K, m0, kTcM, p.Kp, p.vec_a);
+        }
+    }
+    for (int t = t0; t < t1; ++t) {
+        const int z = t / p.mtiles, m0 = (t % p.mtiles) * kTcM;
+        if (z != cur_z) {
+            tc_stage(Bs, p.B + z * p.sb, p.ldb, p.N, p.K, 0, p.N, p.Kp, p.vec_b);
+            for (int n = threadIdx.x; n < p.N; n += blockDim.x) bias_s[n] = p.bias ? p.bias[z * p.sbias + n] : 0.0f;
+            cur_z = z;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+            for (int ks = 0; ks < p.Kp / 16; ++ks) {
+                const uint64_t ad = tc_desc(a0 + ks * 256u, 128u, sbo), bd = tc_desc(b0 + ks * 256u, 128u, sbo);
+                asm volatile("{\n .reg .pred acc;\n setp.ne.b32 acc, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, acc;\n}" ::"r"(tmem),
+                             "l"(ad), "l"(bd), "r"(idesc), "r"(ks > 0 ? 1 : 0)
+                             : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&mbar))
+                         : "memory");
+        }
+        const bool ok = tc_wait(&mbar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            aborted = true;
+            break;
+        }
+        // the MMAs are done with the activation tile: fetch the next one behind the epilogue
+        const bool next = t + 1 < t1;
+        int z1 = 0, m1 = 0;
+        if (next) {
+            z1 = (t + 1) / p.mtiles;
+            m1 = ((t + 1) % p.mtiles) * kTcM;
+            if (async_a) tc_stage_async(As, p.A + z1 * p.sa, p.lda, p.M, m1, kTcM, p.Kp);
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int row = m0 + q * 32 + lane;
+        for (int ch = half; ch < nchunk; ch += 2) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ch * 16);
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                         "%12, %13, %14, %15}, [%16];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                           "=r"(r[14]), "=r"(r[15])
+                         : "r"(taddr)
+                         : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < p.M) {
+                const int n0 = ch * 16;
+                float v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]) + bias_s[n0 + j];
+                if (p.epi == CPM_MLP_EPI_GELU) {
+                    if (p.Z) {
+                        float *zr = p.Z + z * p.sz + (int64_t)row * p.ldz + n0;
+                        if (p.vec_c) {
+#pragma unroll
+                            for (int j = 0; j < 16; j += 4)
+                                *reinterpret_cast<float4 *>(zr + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) zr[j] = v[j];
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = gelu_f(v[j]);
+                }
+                const int64_t o = z * p.sc + (int64_t)row * p.ldc + n0;
+                if (p.c_f32) {
+                    float *cr = static_cast<float *>(p.C) + o;
+                    if (p.vec_c) {
+#pragma unroll
+                        for (int j = 0; j < 16; j += 4)
+                            *reinterpret_cast<float4 *>(cr + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) cr[j] = v[j];
+                    }
+                } else {
+                    __nv_bfloat16 *cr = static_cast<__nv_bfloat16 *>(p.C) + o;
+                    __align__(16) __nv_bfloat16 hb[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) hb[j] = __float2bfloat16(v[j]);
+                    if (p.vec_c) {
+                        reinterpret_cast<uint4 *>(cr)[0] = reinterpret_cast<const uint4 *>(hb)[0];
+                        reinterpret_cast<uint4 *>(cr)[1] = reinterpret_cast<const uint4 *>(hb)[1];
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) cr[j] = hb[j];
+                    }
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        if (next) {
+            if (async_a) asm volatile("cp.async.wait_all;\n" ::: "memory");
+            else {
+                __syncthreads();  // every warp is done with the tile before it is overwritten
+                tc_stage(As, p.A + z1 * p.sa, p.lda, p.M, p.K, m1, kTcM, p.Kp, p.vec_a);
+            }
+        }
+        __syncthreads();
+    }
+    if (aborted) {
+        // record the timeout, then give the issued MMAs another bounded wait before freeing TMEM
+        if (threadIdx.x == 0 && p.err) atomicExch(p.err, 1);
+        tc_wait(&mbar, phase ^ 1u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)p.ncols)
+                     : "memory");
+}
+
 unsigned grid1(int64_t n)
 {
     const int64_t b = (n + 255) / 256;
@@ -320,12 +586,85 @@ unsigned grid1(int64_t n)
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-int launch_gemm(int ta, int tb, GemmArgs &a, int batch, cudaStream_t st)
+// The tensor-core path takes the forward layout (A [M][K], W [N][K]) with
+// N a multiple of 16 up to 256 and K up to 256.
+bool tc_eligible(int ta, int tb, const GemmArgs &a)
+{
+    return ta == 0 && tb == 1 && a.epi != CPM_MLP_EPI_DGELU && a.N >= 16 && a.N <= 256 && a.N % 16 == 0 &&
+           a.K >= 1 && a.K <= 256;
+}
+
+int launch_gemm_tc(const GemmArgs &a, int batch, int *err, cudaStream_t st)
+{
+    TcArgs p{};
+    p.M = a.M;
+    p.N = a.N;
+    p.K = a.K;
+    p.Kp = (a.K + 15) / 16 * 16;
+    p.ncols = 32;
+    while (p.ncols < a.N) p.ncols *= 2;
+    p.A = a.A;
+    p.lda = a.lda;
+    p.sa = a.sa;
+    p.B = a.B;
+    p.ldb = a.ldb;
+    p.sb = a.sb;
+    p.bias = a.bias;
+    p.sbias = a.sbias;
+    p.C = a.C;
+    p.ldc = a.ldc;
+    p.sc = a.sc;
+    p.Z = a.Z;
+    p.ldz = a.ldz;
+    p.sz = a.sz;
+    p.epi = a.epi;
+    p.c_f32 = a.c_f32;
+    p.vec_a = a.vec_a;
+    p.vec_b = a.vec_b;
+    // 16-element runs of C (and Z) start 16-byte aligned
+    p.vec_c = aligned16(a.C) && a.ldc % 8 == 0 && a.sc % 8 == 0 && (!a.Z || (aligned16(a.Z) && a.ldz % 4 == 0 && a.sz % 4 == 0));
+    p.mtiles = (a.M + kTcM - 1) / kTcM;
+    p.tiles = p.mtiles * batch;
+    p.err = err;
+    size_t smem = (size_t)(a.N + kTcM) * p.Kp * 2 + (size_t)a.N * 4;
+    // at most 512 / ncols CTAs may hold TMEM on one SM: pad the shared memory so that no more are resident
+    const int per_sm_tmem = 512 / p.ncols;
+    const size_t floor_smem = per_sm_tmem >= 8 ? 0 : (size_t)(228 * 1024) / (size_t)(per_sm_tmem + 1) + 1024;
+    if (smem < floor_smem) smem = floor_smem;
+    static int sms = 0, max_dyn = 0;
+    if (sms == 0) {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncAttributes fa{};
+        cudaFuncGetAttributes(&fa, gemm_tc_kernel);
+        max_dyn = optin - (int)fa.sharedSizeBytes;
+        if (cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn) != cudaSuccess)
+            max_dyn = 48 * 1024 - (int)fa.sharedSizeBytes;
+        cudaGetLastError();
+    }
+    if (smem > (size_t)max_dyn) return kTcNotApplicable;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemm_tc_kernel, kTcThreads, smem);
+    if (per_sm < 1) per_sm = 1;
+    int grid = sms * per_sm;
+    if (grid > p.tiles) grid = p.tiles;
+    gemm_tc_kernel<<<grid, kTcThreads, smem, st>>>(p);
+    return cudaPeekAtLastError() == cudaSuccess ? CPM_MLP_OK : CPM_MLP_E_CUDA;
+}
+
+int launch_gemm(int ta, int tb, GemmArgs &a, int batch, cudaStream_t st, int *tc_err = nullptr,
+                bool allow_tc = true)
 {
     if (a.M == 0 || a.N == 0) return CPM_MLP_OK;
     // vector loads need 16-byte aligned rows: base, leading dimension and member stride
     a.vec_a = aligned16(a.A) && a.lda % 8 == 0 && a.sa % 8 == 0;
     a.vec_b = aligned16(a.B) && a.ldb % 8 == 0 && a.sb % 8 == 0;
+    if (allow_tc && tc_eligible(ta, tb, a)) {
+        const int rc = launch_gemm_tc(a, batch, tc_err, st);
+        if (rc != kTcNotApplicable) return rc;
+    }
     const dim3 grid((a.N + kBN - 1) / kBN, (a.M + kBM - 1) / kBM, batch);
     if (grid.y > 65535u || batch > 65535) return CPM_MLP_E_INVALID;
     if (ta) {
@@ -431,7 +770,7 @@ int forward(cpm_mlp *h, int rows, bool keep_z)
             a.c_f32 = 1;
             a.epi = CPM_MLP_EPI_NONE;
         }
-        const int rc = launch_gemm(0, 1, a, h->sh.n_members, h->st);
+        const int rc = launch_gemm(0, 1, a, h->sh.n_members, h->st, h->bad + 1);
         if (rc) return fail(h, rc, "forward gemm launch failed");
         ++h->launches;
     }
@@ -512,14 +851,16 @@ int gather(cpm_mlp *h, const float *X, const float *Y, const int32_t *order, int
     return cuda_check(h, cudaPeekAtLastError(), "gather");
 }
 
+// flags: [0] a row index outside the data, [1] a tensor-core wait that timed out
 int check_bad(cpm_mlp *h)
 {
-    int bad = 0;
-    int rc = cuda_check(h, cudaMemcpyAsync(&bad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->st), "read flag");
+    int bad[2] = {0, 0};
+    int rc = cuda_check(h, cudaMemcpyAsync(bad, h->bad, sizeof bad, cudaMemcpyDeviceToHost, h->st), "read flag");
     if (!rc) rc = cuda_check(h, cudaStreamSynchronize(h->st), "sync");
     if (rc) return rc;
-    if (bad) {
-        cudaMemsetAsync(h->bad, 0, sizeof(int), h->st);
+    if (bad[0] || bad[1]) {
+        cudaMemsetAsync(h->bad, 0, sizeof bad, h->st);
+        if (bad[1]) return fail(h, CPM_MLP_E_CUDA, "tensor-core accumulator wait timed out");
         return fail(h, CPM_MLP_E_INVALID, "row index out of range in order[]");
     }
     return CPM_MLP_OK;
@@ -572,7 +913,7 @@ int cpm_mlp_create(const cpm_mlp_shape *shape, const float *init_params, void *c
         rc |= dalloc(h, &h->H[l], (int64_t)E * R * W) | dalloc(h, &h->Z[l], (int64_t)E * R * W);
     rc |= dalloc(h, &h->out, (int64_t)E * R * shape->n_out) | dalloc(h, &h->dP, (int64_t)E * R * shape->n_out);
     rc |= dalloc(h, &h->dZ[0], (int64_t)E * R * W) | dalloc(h, &h->dZ[1], (int64_t)E * R * W);
-    rc |= dalloc(h, &h->loss, E) | dalloc(h, &h->bad, 1);
+    rc |= dalloc(h, &h->loss, E) | dalloc(h, &h->bad, 2);
     rc |= dalloc(h, &h->shift, shape->n_out) | dalloc(h, &h->scale, shape->n_out) | dalloc(h, &h->rmse, shape->n_out);
     rc |= dalloc(h, &h->logm, shape->n_out);
     if (rc) {
@@ -581,7 +922,7 @@ int cpm_mlp_create(const cpm_mlp_shape *shape, const float *init_params, void *c
         return CPM_MLP_E_NOMEM;
     }
     if (cpm_mlp_set_params(h, init_params) != CPM_MLP_OK ||
-        cudaMemsetAsync(h->bad, 0, sizeof(int), h->st) != cudaSuccess) {
+        cudaMemsetAsync(h->bad, 0, 2 * sizeof(int), h->st) != cudaSuccess) {
         release(h);
         delete h;
         return CPM_MLP_E_CUDA;
@@ -676,7 +1017,7 @@ int cpm_mlp_forward(cpm_mlp *h, const float *X, int64_t n_rows, float *out)
                             "copy out");
         if (rc) return rc;
     }
-    return cuda_check(h, cudaStreamSynchronize(h->st), "sync");
+    return check_bad(h);
 }
 
 int cpm_mlp_set_output_transform(cpm_mlp *h, const float *shift, const float *scale, const uint8_t *log_mask,
@@ -717,7 +1058,7 @@ int cpm_mlp_predict(cpm_mlp *h, const float *X, int64_t n_rows, float *mean_out,
         ++h->launches;
     }
     if (int rc = cuda_check(h, cudaPeekAtLastError(), "predict")) return rc;
-    return cuda_check(h, cudaStreamSynchronize(h->st), "sync");
+    return check_bad(h);
 }
 
 uint64_t cpm_mlp_kernel_launches(const cpm_mlp *h) { return h ? h->launches : 0; }

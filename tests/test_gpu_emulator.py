@@ -57,6 +57,11 @@ GEMM_CASES = [
     (5, 300, 130, 2, False, True),
     (200, 7, 300, 2, False, False),
     (16, 256, 1000, 5, False, False),
+    # shapes the tensor-core (tcgen05) forward path takes when (ta, tb) = (0, 1)
+    (300, 256, 256, 5, False, False),
+    (129, 32, 64, 2, True, False),
+    (1000, 16, 256, 3, False, False),
+    (640, 128, 24, 2, False, True),
 ]
 
 
