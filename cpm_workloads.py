@@ -482,3 +482,34 @@ def mlp_init(seed: int, n_members: int, sizes) -> np.ndarray:
             parts.append(np.zeros(o))
         out.append(np.concatenate(parts))
     return np.asarray(out, dtype=np.float32)
+
+
+# --------------------------------------------------------------------------
+# cell sorting (two cell types with differential adhesion)
+# --------------------------------------------------------------------------
+
+def sorting_2d(seed: int = 1, n: int = 128, edge: int = 8, a: int = 4, c: int = 2, P: int = 1) -> Workload:
+    """Cell sorting by differential adhesion (Results, Fig. 4, after Graner &
+    Glazier): a confluent 2D n x n periodic tissue, Moore-8, tiled by
+    edge x edge square cells (no medium), each cell type 1 ("dark") or 2
+    ("light") at random in equal numbers; J(d,d) = 2, J(l,l) = 14,
+    J(l,d) = 11, J with the medium 16, V_t = edge^2, lambda_V = 1, T = 10."""
+    rng = np.random.default_rng(seed)
+    k = n // edge
+    n_cells = k * k
+    ids = np.arange(1, n_cells + 1, dtype=np.int32).reshape(k, k)
+    lat = np.repeat(np.repeat(ids, edge, axis=0), edge, axis=1)[None]
+    types = np.array([1] * (n_cells // 2) + [2] * (n_cells - n_cells // 2), dtype=np.uint8)
+    rng.shuffle(types)
+    ct = np.concatenate([[0], types]).astype(np.uint8)
+    J, lv, vt, lp, at, la, ma = _params()
+    _sym(J, 1, 1, 2)
+    _sym(J, 2, 2, 14)
+    _sym(J, 1, 2, 11)
+    _sym(J, 0, 1, 16)
+    _sym(J, 0, 2, 16)
+    for t in (1, 2):
+        lv[t] = 1
+        vt[t] = edge * edge
+    return Workload("sorting_%d" % seed, 2, n, n, 1, J, lv, vt, lp, at, la, ma, 10.0, 1, a, c, P, seed, 3, lat, ct,
+                    None, 1)
