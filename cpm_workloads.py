@@ -62,6 +62,12 @@ class Workload:
     n_mcs: int = 1
     tile: int = 0            # tiled schedule: tile edge T (0: global rounds)
     tile_cycles: int = 1     # tiled schedule: tile cycles per MCS
+    # motility terms (Eq. 4 to Eq. 7); None = off
+    chem_field: Optional[np.ndarray] = None   # int16 [nz, ny, nx, dim]: the field C in Q14 (16384 = 1)
+    lambda_chem: Optional[np.ndarray] = None  # int32 [MAX_TYPES], scaled
+    lambda_pers: Optional[np.ndarray] = None  # int32 [MAX_TYPES], scaled
+    mu_pers: Optional[np.ndarray] = None      # float64 [MAX_TYPES]: persistence strength mu
+    dt_pers: Optional[np.ndarray] = None      # int32 [MAX_TYPES]: look-back of the update, MCS
 
     @property
     def n_cells(self) -> int:
@@ -74,6 +80,14 @@ class Workload:
     @property
     def act_on(self) -> bool:
         return bool(np.any(self.lambda_act != 0))
+
+    @property
+    def pers_on(self) -> bool:
+        return self.lambda_pers is not None and bool(np.any(self.lambda_pers != 0))
+
+    @property
+    def chem_on(self) -> bool:
+        return self.chem_field is not None and self.lambda_chem is not None and bool(np.any(self.lambda_chem != 0))
 
     def replace(self, **kw) -> "Workload":
         return dataclasses.replace(self, **kw)
@@ -513,3 +527,50 @@ def sorting_2d(seed: int = 1, n: int = 128, edge: int = 8, a: int = 4, c: int = 
         vt[t] = edge * edge
     return Workload("sorting_%d" % seed, 2, n, n, 1, J, lv, vt, lp, at, la, ma, 10.0, 1, a, c, P, seed, 3, lat, ct,
                     None, 1)
+
+
+# --------------------------------------------------------------------------
+# motility fields and settings (Eq. 4 to Eq. 7)
+# --------------------------------------------------------------------------
+
+def circular_field(nx: int, ny: int, nz: int = 1, dim: int = 2) -> np.ndarray:
+    """The paper's 2D chemotaxis field (Table 1, Fig. 6A): unit vectors at
+    90 degrees to the radial vector from the lattice centre (a circular
+    flow), in Q14 int16 components; the same in every z plane for 3D (z
+    component 0); the centre site gets (0, 0)."""
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    rx, ry = x - (nx - 1) / 2.0, y - (ny - 1) / 2.0
+    r = np.hypot(rx, ry)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        vx = np.where(r > 0, -ry / r, 0.0)
+        vy = np.where(r > 0, rx / r, 0.0)
+    f = np.zeros((nz, ny, nx, dim), dtype=np.int16)
+    f[..., 0] = np.round(vx * 16384).astype(np.int16)[None]
+    f[..., 1] = np.round(vy * 16384).astype(np.int16)[None]
+    return f
+
+
+def uniform_field(shape, dim: int, direction) -> np.ndarray:
+    """A constant field of unit vectors along ``direction`` (Q14 int16)."""
+    d = np.asarray(direction, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    f = np.zeros(tuple(shape) + (dim,), dtype=np.int16)
+    for k in range(dim):
+        f[..., k] = int(round(d[k] * 16384))
+    return f
+
+
+def with_motility(w: Workload, chem=None, lambda_chem=0, lambda_pers=0, mu=0.0, dt=1, types=None) -> Workload:
+    """w with the chemotaxis field ``chem`` (or None) and the same
+    lambda_chem, lambda_pers, mu and dt for every cell type in ``types``
+    (all cell types by default)."""
+    types = range(1, MAX_TYPES) if types is None else types
+    lc = np.zeros(MAX_TYPES, dtype=np.int32)
+    lp = np.zeros(MAX_TYPES, dtype=np.int32)
+    mu_ = np.zeros(MAX_TYPES, dtype=np.float64)
+    dt_ = np.zeros(MAX_TYPES, dtype=np.int32)
+    for t in types:
+        lc[t], lp[t], mu_[t], dt_[t] = lambda_chem, lambda_pers, mu, dt
+    return w.replace(chem_field=chem, lambda_chem=lc if chem is not None else None,
+                     lambda_pers=lp if lambda_pers else None, mu_pers=mu_ if lambda_pers else None,
+                     dt_pers=dt_ if lambda_pers else None)

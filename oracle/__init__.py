@@ -59,6 +59,15 @@ class Params(ctypes.Structure):
         ("cell_type", ctypes.POINTER(ctypes.c_uint8)),
         ("tile", ctypes.c_int32),
         ("tile_cycles", ctypes.c_int32),
+        ("chem_field", ctypes.POINTER(ctypes.c_int16)),
+        ("lambda_chem", ctypes.c_int32 * MAXT),
+        ("lambda_pers", ctypes.c_int32 * MAXT),
+        ("mu_pers", ctypes.c_double * MAXT),
+        ("dt_pers", ctypes.c_int32 * MAXT),
+        ("pers_dir", ctypes.POINTER(ctypes.c_double)),
+        ("pers_hist", ctypes.POINTER(ctypes.c_double)),
+        ("pers_hist_len", ctypes.c_int32),
+        ("pers_t0", ctypes.c_int64),
     ]
 
 
@@ -73,7 +82,13 @@ def lib():
         i32p, u8p, i64p, u32p = P(ctypes.c_int32), P(ctypes.c_uint8), P(ctypes.c_int64), P(ctypes.c_uint32)
         _lib.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
         _lib.orc_serial_run.argtypes = [P(Params), i32p, u8p, i32p, i32p, ctypes.c_int64,
-                                        P(ctypes.c_uint64), i64p]
+                                        P(ctypes.c_uint64), i64p, i64p]
+        f64p = P(ctypes.c_double)
+        _lib.orc_motility.argtypes = [P(Params), i32p, ctypes.c_int64, ctypes.c_int, i64p, f64p]
+        _lib.orc_centroids.argtypes = [P(Params), i32p, f64p]
+        _lib.orc_centroids.restype = None
+        _lib.orc_pers_update.argtypes = [P(Params), i32p, ctypes.c_int64]
+        _lib.orc_pers_update.restype = None
         _lib.orc_replay_run.argtypes = [P(Params), i32p, u8p, i32p, i32p, i64p, i32p, ctypes.c_int64, i64p]
         _lib.orc_replay_round.argtypes = [P(Params), i32p, u8p, i32p, i32p, ctypes.c_int64, ctypes.c_int32,
                                           ctypes.c_int32, i64p, ctypes.c_int64, i64p]
@@ -116,7 +131,13 @@ class State:
                         else np.ascontiguousarray(w.act, dtype=np.uint8).copy())
         else:
             self.act = None
-        self.params = make_params(w, self.cell_type)
+        self.chem = (np.ascontiguousarray(w.chem_field, dtype=np.int16).copy()
+                     if getattr(w, "chem_field", None) is not None else None)
+        pers = getattr(w, "pers_on", False)
+        self.pers_len = int(np.max(w.dt_pers)) + 1 if pers else 0
+        self.pers_dir = np.zeros((w.n_cells + 1, 3)) if pers else None
+        self.pers_hist = np.full((max(self.pers_len, 1), w.n_cells + 1, 3), np.nan) if pers else None
+        self.params = make_params(w, self.cell_type, self)
         self.V = np.zeros(w.n_cells + 1, dtype=np.int32)
         self.A = np.zeros(w.n_cells + 1, dtype=np.int32)
         if recount:
@@ -124,6 +145,8 @@ class State:
                               _ptr(self.V, ctypes.c_int32), _ptr(self.A, ctypes.c_int32))
         self.t = 0
         self.sp = 0
+        if pers:  # the centroids at the start: the first look-back point
+            lib().orc_pers_update(ctypes.byref(self.params), _ptr(self.lattice, ctypes.c_int32), 0)
         self.rng = (ctypes.c_uint64 * 4)()
         lib().orc_xoshiro_seed(ctypes.c_uint64(w.seed), self.rng)
         self.accepts = 0
@@ -131,12 +154,14 @@ class State:
     # ----------------------------------------------------------------
     def serial_run(self, n_mcs: int) -> int:
         acc = ctypes.c_int64(0)
+        t = ctypes.c_int64(self.t)
         rc = lib().orc_serial_run(ctypes.byref(self.params), _ptr(self.lattice, ctypes.c_int32),
                                   _ptr(self.act, ctypes.c_uint8), _ptr(self.V, ctypes.c_int32),
-                                  _ptr(self.A, ctypes.c_int32), n_mcs, self.rng, ctypes.byref(acc))
+                                  _ptr(self.A, ctypes.c_int32), n_mcs, self.rng, ctypes.byref(t),
+                                  ctypes.byref(acc))
         if rc != 0:
             raise RuntimeError("orc_serial_run failed: %d" % rc)
-        self.t += n_mcs
+        self.t = t.value
         self.accepts += acc.value
         return acc.value
 
@@ -176,6 +201,19 @@ class State:
             raise RuntimeError("orc_replay_round failed: %d" % rc)
         return acc.value
 
+    def motility(self, j: int, n_idx: int):
+        """Motility terms of the copy from neighbour n_idx of j into j: (Q4 as
+        the replay applies them, real as the serial chain does)."""
+        q, r = ctypes.c_int64(0), ctypes.c_double(0.0)
+        lib().orc_motility(ctypes.byref(self.params), _ptr(self.lattice, ctypes.c_int32), j, n_idx,
+                           ctypes.byref(q), ctypes.byref(r))
+        return q.value, r.value
+
+    def centroids(self) -> np.ndarray:
+        X = np.zeros((self.w.n_cells + 1, 3))
+        lib().orc_centroids(ctypes.byref(self.params), _ptr(self.lattice, ctypes.c_int32), _ptr(X, ctypes.c_double))
+        return X
+
     def recount(self):
         V = np.zeros_like(self.V)
         A = np.zeros_like(self.A)
@@ -196,7 +234,7 @@ class State:
         return {k: x.value for k, x in zip(keys, r)}
 
 
-def make_params(w, cell_type: np.ndarray) -> Params:
+def make_params(w, cell_type: np.ndarray, state=None) -> Params:
     p = Params()
     p.dim, p.nx, p.ny, p.nz = w.dim, w.nx, w.ny, w.nz
     for a in range(MAXT):
@@ -216,6 +254,22 @@ def make_params(w, cell_type: np.ndarray) -> Params:
     p.cell_type = cell_type.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
     p.tile = int(getattr(w, "tile", 0))
     p.tile_cycles = int(getattr(w, "tile_cycles", 1))
+    if state is not None and state.chem is not None:
+        p.chem_field = _ptr(state.chem, ctypes.c_int16)
+    for name in ("lambda_chem", "lambda_pers", "dt_pers"):
+        v = getattr(w, name, None)
+        if v is not None:
+            arr = getattr(p, name)
+            for a in range(MAXT):
+                arr[a] = int(v[a])
+    if getattr(w, "mu_pers", None) is not None:
+        for a in range(MAXT):
+            p.mu_pers[a] = float(w.mu_pers[a])
+    if state is not None and state.pers_dir is not None:
+        p.pers_dir = _ptr(state.pers_dir, ctypes.c_double)
+        p.pers_hist = _ptr(state.pers_hist, ctypes.c_double)
+        p.pers_hist_len = state.pers_len
+        p.pers_t0 = 0
     return p
 
 

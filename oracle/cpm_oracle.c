@@ -58,6 +58,16 @@ typedef struct {
     const uint8_t *cell_type; /* n_cells + 1 entries, [0] = medium */
     int32_t tile;             /* 0: global rounds; T > 0: tiled epochs of edge T */
     int32_t tile_cycles;      /* P_T: tile cycles per MCS (divides P) */
+    /* motility terms (Eq. 4 to Eq. 7); zero / NULL when unused */
+    const int16_t *chem_field;  /* [site][dim] components of the field C in Q14 (16384 = 1) */
+    int32_t lambda_chem[ORC_MAXT];
+    int32_t lambda_pers[ORC_MAXT];
+    double mu_pers[ORC_MAXT];
+    int32_t dt_pers[ORC_MAXT];  /* look-back of the persistence update, MCS (>= 1 where lambda_pers != 0) */
+    double *pers_dir;           /* state: [n_cells + 1][3] persistence directions p_hat */
+    double *pers_hist;          /* state: [pers_hist_len][n_cells + 1][3] centroids, NaN for absent cells */
+    int32_t pers_hist_len;      /* > max dt_pers */
+    int64_t pers_t0;            /* MCS of the first recorded centroids */
 } orc_params;
 
 /* ------------------------------------------------------------------ */
@@ -222,6 +232,174 @@ static int64_t delta_h_int(const orc_params *p, const int32_t *lat, int64_t j, i
 }
 
 /* ------------------------------------------------------------------ */
+/* Motility terms (Eq. 4 chemotaxis, Eq. 5 persistence).  A copy from the */
+/* source i into the target j moves the cell sigma_i (or, when sigma_i is */
+/* the medium, sigma_j) along d = j - i; the term is -lambda(tau) x.v     */
+/* with x = d / |d| and v the field at i (Eq. 4) or the cell's direction  */
+/* p_hat (Eq. 5): copies along v become more likely, as the paper         */
+/* describes (the printed sign would make them less likely).  In Q4       */
+/* units it is floor(e), e formed by exactly this sequence of rounded     */
+/* double operations: chemotaxis e = ((double)(-16 lambda (d.C_q)) /      */
+/* 16384) * (1/sqrt(|d|^2)); persistence s = d_x p_x + d_y p_y + d_z p_z  */
+/* (left to right), e = (s * (double)(-16 lambda)) * (1/sqrt(|d|^2)).      */
+/* ------------------------------------------------------------------ */
+static int motility_enabled(const orc_params *p)
+{
+    for (int t = 0; t < ORC_MAXT; t++)
+        if ((p->chem_field && p->lambda_chem[t] != 0) || (p->pers_dir && p->lambda_pers[t] != 0)) return 1;
+    return 0;
+}
+
+static int pers_enabled(const orc_params *p)
+{
+    if (!p->pers_dir || !p->pers_hist) return 0;
+    for (int t = 0; t < ORC_MAXT; t++)
+        if (p->lambda_pers[t] != 0) return 1;
+    return 0;
+}
+
+static double inv_len(int k) { return 1.0 / sqrt((double)k); }
+
+/* copy direction d = j - i for source i = j + off (the neighbour offset) */
+static void copy_dir(const int32_t o[3], int d[3], int *k)
+{
+    d[0] = -o[0];
+    d[1] = -o[1];
+    d[2] = -o[2];
+    *k = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+}
+
+static int64_t motility_q(const orc_params *p, int64_t i, int32_t si, int32_t sj, const int32_t o[3])
+{
+    int32_t m = si > 0 ? si : sj;
+    int tp = type_of(p, m);
+    int d[3], k;
+    copy_dir(o, d, &k);
+    int64_t dh = 0;
+    if (p->chem_field && p->lambda_chem[tp] != 0) {
+        const int16_t *c = p->chem_field + i * p->dim;
+        int64_t dc = (int64_t)d[0] * c[0] + (int64_t)d[1] * c[1] + (p->dim == 3 ? (int64_t)d[2] * c[2] : 0);
+        double e = (double)(-16 * (int64_t)p->lambda_chem[tp] * dc) / 16384.0;
+        e = e * inv_len(k);
+        dh += (int64_t)floor(e);
+    }
+    if (p->pers_dir && p->lambda_pers[tp] != 0 && m > 0) {
+        const double *ph = p->pers_dir + 3 * (int64_t)m;
+        double sdot = (double)d[0] * ph[0];
+        sdot = sdot + (double)d[1] * ph[1];
+        sdot = sdot + (double)d[2] * ph[2];
+        double e = sdot * (double)(-16 * (int64_t)p->lambda_pers[tp]);
+        e = e * inv_len(k);
+        dh += (int64_t)floor(e);
+    }
+    return dh;
+}
+
+static double motility_real(const orc_params *p, int64_t i, int32_t si, int32_t sj, const int32_t o[3])
+{
+    int32_t m = si > 0 ? si : sj;
+    int tp = type_of(p, m);
+    int d[3], k;
+    copy_dir(o, d, &k);
+    double len = sqrt((double)k), dh = 0.0;
+    if (p->chem_field && p->lambda_chem[tp] != 0) {
+        const int16_t *c = p->chem_field + i * p->dim;
+        double dc = d[0] * (c[0] / 16384.0) + d[1] * (c[1] / 16384.0) + (p->dim == 3 ? d[2] * (c[2] / 16384.0) : 0.0);
+        dh -= p->lambda_chem[tp] * dc / len;
+    }
+    if (p->pers_dir && p->lambda_pers[tp] != 0 && m > 0) {
+        const double *ph = p->pers_dir + 3 * (int64_t)m;
+        dh -= p->lambda_pers[tp] * (d[0] * ph[0] + d[1] * ph[1] + d[2] * ph[2]) / len;
+    }
+    return dh;
+}
+
+/* Centroids of every cell (Eq. 10) in one periodic image: the cell's first
+ * site in raster order plus the mean minimal-image offset from it; NaN for
+ * a cell without sites.  X has (n_cells + 1) x 3 entries. */
+void orc_centroids(const orc_params *p, const int32_t *lat, double *X)
+{
+    int64_t nc = p->n_cells + 1, N = (int64_t)p->nx * p->ny * p->nz, plane = (int64_t)p->nx * p->ny;
+    int64_t *anchor = (int64_t *)malloc(sizeof(int64_t) * nc);
+    int64_t *sums = (int64_t *)calloc((size_t)(4 * nc), sizeof(int64_t));
+    int64_t L[3] = {p->nx, p->ny, p->nz};
+    for (int64_t c = 0; c < nc; c++) anchor[c] = -1;
+    for (int64_t x = 0; x < N; x++) {
+        int32_t s = lat[x];
+        if (s <= 0) continue;
+        if (anchor[s] < 0) anchor[s] = x;
+        int64_t a = anchor[s];
+        int64_t pc[3] = {x % p->nx, (x / p->nx) % p->ny, x / plane};
+        int64_t ac[3] = {a % p->nx, (a / p->nx) % p->ny, a / plane};
+        for (int d = 0; d < 3; d++) {
+            int64_t o = wrap(pc[d] - ac[d] + L[d] / 2, L[d]) - L[d] / 2;
+            sums[4 * s + d] += o;
+        }
+        sums[4 * s + 3] += 1;
+    }
+    for (int64_t c = 0; c < nc; c++) {
+        if (anchor[c] < 0 || c == 0) {
+            X[3 * c] = X[3 * c + 1] = X[3 * c + 2] = NAN;
+            continue;
+        }
+        int64_t a = anchor[c];
+        int64_t ac[3] = {a % p->nx, (a / p->nx) % p->ny, a / plane};
+        double v = (double)sums[4 * c + 3];
+        for (int d = 0; d < 3; d++) X[3 * c + d] = (double)ac[d] + (double)sums[4 * c + d] / v;
+    }
+    free(anchor);
+    free(sums);
+}
+
+/* Persistence update (Eq. 6 and Eq. 7) at the end of an MCS, time t: record
+ * the centroids; for every cell with a look-back dt whose centroid is known
+ * at t and t - dt, u = D / |D| for the minimal-image displacement D,
+ * p = (1 - mu) u + mu p_hat, p_hat = p / |p| (each product and sum rounded
+ * in this order, no fused operations).  A zero displacement or an unknown
+ * centroid leaves p_hat unchanged. */
+void orc_pers_update(const orc_params *p, const int32_t *lat, int64_t t)
+{
+    if (!pers_enabled(p)) return;
+    int64_t nc = p->n_cells + 1;
+    double *X = p->pers_hist + 3 * nc * (t % p->pers_hist_len);
+    orc_centroids(p, lat, X);
+    double L[3] = {p->nx, p->ny, p->nz};
+    for (int64_t c = 1; c < nc; c++) {
+        int tp = p->cell_type[c];
+        int dt = p->dt_pers[tp];
+        if (p->lambda_pers[tp] == 0 || dt < 1 || t - dt < p->pers_t0) continue;
+        const double *Xo = p->pers_hist + 3 * nc * ((t - dt) % p->pers_hist_len) + 3 * c;
+        const double *Xn = X + 3 * c;
+        if (isnan(Xo[0]) || isnan(Xn[0])) continue;
+        double D[3];
+        for (int d = 0; d < 3; d++) {
+            double v = Xn[d] - Xo[d];
+            D[d] = v - L[d] * rint(v / L[d]);
+        }
+        double n2 = D[0] * D[0];
+        n2 = n2 + D[1] * D[1];
+        n2 = n2 + D[2] * D[2];
+        if (n2 == 0.0) continue;
+        double n = sqrt(n2), a = 1.0 - p->mu_pers[tp], mu = p->mu_pers[tp];
+        double *ph = p->pers_dir + 3 * c, q[3];
+        for (int d = 0; d < 3; d++) {
+            double u = D[d] / n;
+            double x = a * u, y = mu * ph[d];
+            q[d] = x + y;
+        }
+        double m2 = q[0] * q[0];
+        m2 = m2 + q[1] * q[1];
+        m2 = m2 + q[2] * q[2];
+        if (m2 == 0.0) {
+            ph[0] = ph[1] = ph[2] = 0.0;
+            continue;
+        }
+        double m = sqrt(m2);
+        for (int d = 0; d < 3; d++) ph[d] = q[d] / m;
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* Act model (Eq. 8 and Eq. 9).  GM(x) is the geometric mean of Act     */
 /* over x and those of its Moore neighbours that belong to the same     */
 /* cell; it is 0 for medium sites and whenever one of those Act values  */
@@ -368,6 +546,19 @@ static void decay_act(const orc_params *p, uint8_t *act)
         if (act[x] > 0) act[x] -= 1;
 }
 
+/* Exposed for tests: the motility terms of the copy from neighbour n_idx of
+ * j into j, in Q4 (as the replay applies them) and in real units (as the
+ * serial chain does). */
+int orc_motility(const orc_params *p, const int32_t *lat, int64_t j, int n_idx, int64_t *dh_q, double *dh_real)
+{
+    int32_t off[26][3];
+    orc_neighbour_offsets(p->dim, off);
+    int64_t i = neighbour(p, j, off[n_idx]);
+    *dh_q = motility_q(p, i, lat[i], lat[j], off[n_idx]);
+    *dh_real = motility_real(p, i, lat[i], lat[j], off[n_idx]);
+    return 0;
+}
+
 /* Exposed for tests: every energy term of one attempt, target j, source its
  * neighbour number n_idx.  Tallies are read from V and A.  */
 int orc_delta_h(const orc_params *p, const int32_t *lat, const uint8_t *act, const int32_t *V,
@@ -403,12 +594,13 @@ int orc_delta_h(const orc_params *p, const int32_t *lat, const uint8_t *act, con
 /* (a) the serial CPM                                                  */
 /* ================================================================== */
 int orc_serial_run(const orc_params *p, int32_t *lat, uint8_t *act, int32_t *V, int32_t *A,
-                   int64_t n_mcs, uint64_t rng[4], int64_t *accepts)
+                   int64_t n_mcs, uint64_t rng[4], int64_t *t_io, int64_t *accepts)
 {
     int32_t off[26][3];
     int nb = orc_neighbour_offsets(p->dim, off);
     int64_t N = (int64_t)p->nx * p->ny * p->nz;
     int use_act = act_enabled(p) && act != NULL;
+    int use_mot = motility_enabled(p);
     int64_t acc = 0;
     for (int64_t t = 0; t < n_mcs; t++) {
         if (use_act) decay_act(p, act);
@@ -423,6 +615,7 @@ int orc_serial_run(const orc_params *p, int32_t *lat, uint8_t *act, int32_t *V, 
             double dh = (double)delta_h_int(p, lat, j, si, sj, si > 0 ? V[si] : 0, sj > 0 ? V[sj] : 0,
                                             si > 0 ? A[si] : 0, sj > 0 ? A[sj] : 0, nb, off, &mi, &mj);
             if (use_act) dh += delta_h_act_real(p, lat, act, i, j, si, sj, nb, off);
+            if (use_mot) dh += motility_real(p, i, si, sj, off[n]);
             if (!(dh <= 0.0 || rand_unit(rng) < exp(-dh / p->T))) continue;
             lat[j] = si;
             if (si > 0) { V[si] += 1; A[si] += nb - 2 * mi; }
@@ -430,7 +623,9 @@ int orc_serial_run(const orc_params *p, int32_t *lat, uint8_t *act, int32_t *V, 
             if (use_act) act[j] = si > 0 ? (uint8_t)p->max_act[type_of(p, si)] : 0;
             acc++;
         }
+        if (pers_enabled(p)) orc_pers_update(p, lat, (t_io ? *t_io : 0) + t + 1);
     }
+    if (t_io) *t_io += n_mcs;
     if (accepts) *accepts = acc;
     return 0;
 }
@@ -525,6 +720,7 @@ static int replay_round(const orc_params *p, const orc_tables *tb, int32_t *lat,
     int32_t off[26][3];
     int nb = orc_neighbour_offsets(p->dim, off);
     int use_act = act_enabled(p) && act != NULL;
+    int use_mot = motility_enabled(p);
     int s = p->a / p->c;
     int C = ipow(p->c, p->dim);
     int32_t perm[27];
@@ -559,6 +755,7 @@ static int replay_round(const orc_params *p, const orc_tables *tb, int32_t *lat,
         int64_t dhq = 16 * delta_h_int(p, lat, j, si, sj, si > 0 ? Vs[si] : 0, sj > 0 ? Vs[sj] : 0,
                                        si > 0 ? As[si] : 0, sj > 0 ? As[sj] : 0, nb, off, &mi, &mj);
         if (use_act) dhq += delta_h_act_q(p, tb, lat, act, i, j, si, sj, nb, off);
+        if (use_mot) dhq += motility_q(p, i, si, sj, off[n]);
         int ok = dhq <= 0 || (dhq < tb->L && w2 < tb->thr[dhq]);
         if (!ok) continue;
         lat[j] = si;
@@ -760,6 +957,11 @@ static int check_params(const orc_params *p)
         int T = p->tile;
         if (T % p->a || p->nx % (2 * T) || p->ny % (2 * T) || (p->dim == 3 && p->nz % (2 * T))) return -1;
         if (p->tile_cycles < 1 || p->P % p->tile_cycles) return -1;
+        if (motility_enabled(p)) return -1; /* the tiled schedule has no motility terms */
+    }
+    if (pers_enabled(p)) {
+        for (int t = 0; t < ORC_MAXT; t++)
+            if (p->lambda_pers[t] != 0 && (p->dt_pers[t] < 1 || p->dt_pers[t] >= p->pers_hist_len)) return -1;
     }
     return 0;
 }
@@ -787,7 +989,11 @@ int orc_replay_run(const orc_params *p, int32_t *lat, uint8_t *act, int32_t *V, 
             tables_free(&tb);
             return -1;
         }
-        if (++sp == per_mcs) { sp = 0; t++; }
+        if (++sp == per_mcs) {
+            sp = 0;
+            t++;
+            if (pers_enabled(p)) orc_pers_update(p, lat, t);
+        }
     }
     *t_io = t;
     *sp_io = sp;
