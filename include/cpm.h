@@ -115,6 +115,18 @@ typedef struct cpm_config {
     int64_t t0;                  /* MCS index of the first MCS to run (>= 0) */
     int32_t tile;                /* 0: global rounds; T > 0: tiled schedule with tiles of edge T */
     int32_t tile_cycles;         /* tiled schedule: tile cycles per MCS (P_T, divides P) */
+    /* Motility terms (Methods Eq. 4 to Eq. 7), global schedule only; all zero /
+     * NULL = off.  A copy from source i into target j moves the cell sigma_i
+     * (sigma_j when sigma_i is the medium) along d = j - i and adds
+     * floor(-16 lambda (d . v) / |d|) in 1/16 energy units, v being the field
+     * at i (chemotaxis) or the moving cell's persistence direction p_hat;
+     * copies along v become more likely. */
+    const int16_t *chem_field;   /* host, nx*ny*nz*dim int16: the field C per site (components innermost)
+                                    in Q14 (16384 = 1), or NULL */
+    int32_t lambda_chem[CPM_MAX_TYPES];        /* chemotaxis weight per type, scaled */
+    int32_t lambda_pers[CPM_MAX_TYPES];        /* persistence weight per type, scaled */
+    double mu_pers[CPM_MAX_TYPES];             /* persistence memory mu in [0, 1] (Eq. 6) */
+    int32_t dt_pers[CPM_MAX_TYPES];            /* look-back in MCS, 1..255 where lambda_pers != 0 */
 } cpm_config;
 
 typedef struct cpm_stats_t {
@@ -160,6 +172,16 @@ int cpm_read_act(cpm_handle *h, uint8_t *dst, int dst_is_device);
  * -1..n_cells; obstacle sites must stay where they are) and recompute the
  * tallies on the device.  Act values and the position are kept. */
 int cpm_load_lattice(cpm_handle *h, const int32_t *src, int src_is_device);
+
+/* Copy the persistence directions p_hat, (n_cells + 1) x 3 doubles (x, y,
+ * z; zeros before the first update, for absent cells and without the
+ * persistence term) to a host array.  p_hat is updated at the end of every
+ * MCS (Eq. 6, Eq. 7) from the cell centroids (Eq. 10) dt_pers MCS apart:
+ * u = D / |D| for the minimal-image displacement D, p = (1 - mu) u +
+ * mu p_hat, p_hat = p / |p|, every product, sum, quotient and root rounded
+ * once in that order; a zero displacement or an absent cell leaves p_hat.
+ * Synchronises the stream. */
+int cpm_read_persistence(cpm_handle *h, double *dir);
 
 /* Counters and moments of the tallies.  Synchronises the stream. */
 int cpm_stats(cpm_handle *h, cpm_stats_t *out);

@@ -39,6 +39,11 @@ class Config(ctypes.Structure):
         ("t0", ctypes.c_int64),
         ("tile", ctypes.c_int32),
         ("tile_cycles", ctypes.c_int32),
+        ("chem_field", ctypes.POINTER(ctypes.c_int16)),
+        ("lambda_chem", ctypes.c_int32 * MAX_TYPES),
+        ("lambda_pers", ctypes.c_int32 * MAX_TYPES),
+        ("mu_pers", ctypes.c_double * MAX_TYPES),
+        ("dt_pers", ctypes.c_int32 * MAX_TYPES),
     ]
 
 
@@ -64,6 +69,7 @@ _SIGNATURES = {
     "cpm_read_act": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "cpm_load_lattice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "cpm_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
+    "cpm_read_persistence": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "cpm_verify": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "cpm_kernel_launches": (ctypes.c_int64, [ctypes.c_void_p]),
     "cpm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -187,6 +193,19 @@ def make_config(w, keep: list) -> Config:
     c.t0 = 0
     c.tile = int(getattr(w, "tile", 0))
     c.tile_cycles = int(getattr(w, "tile_cycles", 1))
+    if getattr(w, "chem_field", None) is not None:
+        f = np.ascontiguousarray(w.chem_field, dtype=np.int16)
+        keep.append(f)
+        c.chem_field = f.ctypes.data_as(ctypes.POINTER(ctypes.c_int16))
+    for name in ("lambda_chem", "lambda_pers", "dt_pers"):
+        v = getattr(w, name, None)
+        if v is not None:
+            arr = getattr(c, name)
+            for a in range(MAX_TYPES):
+                arr[a] = int(v[a])
+    if getattr(w, "mu_pers", None) is not None:
+        for a in range(MAX_TYPES):
+            c.mu_pers[a] = float(w.mu_pers[a])
     return c
 
 
@@ -235,6 +254,12 @@ class Sim:
             out = np.empty((self.w.nz, self.w.ny, self.w.nx), dtype=np.uint8)
         p, dev = _ptr(out)
         self._check(self.lib.cpm_read_act(self.h, ctypes.c_void_p(p), dev))
+        return out
+
+    def read_persistence(self):
+        """Persistence directions p_hat, (n_cells + 1) x 3 float64."""
+        out = np.zeros((self.w.n_cells + 1, 3))
+        self._check(self.lib.cpm_read_persistence(self.h, ctypes.c_void_p(out.ctypes.data)))
         return out
 
     def load_lattice(self, src):

@@ -43,6 +43,16 @@ struct cpm_handle {
     int *error_flag = nullptr;
     bool shared_tables = false;  // thr / ln_tab / expq belong to a batch's table cache
     double v_ref = 0.0, a_ref = 0.0;  // V_t, A_t of cell 1's type (scales of the summary statistics)
+    // motility (Eq. 4 to Eq. 7)
+    int16_t *chem = nullptr;          // field, dim int16 per site
+    bool pers = false;
+    PersParams pp{};
+    double *pers_dir = nullptr;       // (n_cells + 1) x 3
+    double *pers_hist = nullptr;      // H x (n_cells + 1) x 3 centroids
+    int32_t pers_H = 0;
+    ObserveItem *pers_item = nullptr; // one observation item for this lattice
+    int64_t *pers_cells = nullptr;    // observation rows, (n_cells + 1) x kObsFields
+    int64_t *pers_member = nullptr;   // [2]
     // position
     int64_t t = 0;
     int32_t sp = 0;
@@ -118,6 +128,20 @@ int validate(const cpm_config *c)
         if (c->lambda_v[a] < 0 || c->lambda_p[a] < 0 || c->lambda_act[a] < 0)
             return fail(nullptr, CPM_E_INVALID, "lambdas must be >= 0");
     }
+    bool motility = c->chem_field != nullptr;
+    for (int a = 0; a < CPM_MAX_TYPES; a++) {
+        if (c->lambda_pers[a] != 0) {
+            motility = true;
+            if (c->dt_pers[a] < 1 || c->dt_pers[a] > 255)
+                return fail(nullptr, CPM_E_INVALID, "dt_pers must be in 1..255 where lambda_pers != 0");
+            if (!(c->mu_pers[a] >= 0.0 && c->mu_pers[a] <= 1.0))
+                return fail(nullptr, CPM_E_INVALID, "mu_pers must be in [0, 1]");
+        }
+        if (c->lambda_chem[a] < -(1 << 24) || c->lambda_chem[a] > (1 << 24) || c->lambda_pers[a] < -(1 << 24) ||
+            c->lambda_pers[a] > (1 << 24))
+            return fail(nullptr, CPM_E_INVALID, "motility weights out of range");
+    }
+    if (motility && c->tile > 0) return fail(nullptr, CPM_E_INVALID, "motility terms need the global schedule");
     if (c->t0 < 0) return fail(nullptr, CPM_E_INVALID, "t0 must be >= 0");
     if (c->tile < 0) return fail(nullptr, CPM_E_INVALID, "tile must be >= 0");
     if (c->tile > 0) {
@@ -191,6 +215,19 @@ int reset_tallies(cpm_handle *h)
     return CPM_OK;
 }
 
+// Persistence update at the end of the MCS that brought the handle to time h->t
+// (and at creation): observe the lattice, record the centroids, update p_hat.
+int pers_step(cpm_handle *h)
+{
+    CUDA_TRY(h, launch_observe(h->dim, h->pers_item, 1, (int64_t)h->n_sites, h->pers_cells, h->pers_member,
+                               h->stream));
+    CUDA_TRY(h, launch_pers_update(h->pers_cells, h->n_cells, (uint32_t)h->cfg.nx, (uint32_t)h->cfg.ny,
+                                   (uint32_t)h->cfg.nz, h->cell_type, h->pp, h->pers_hist, h->pers_H, h->t,
+                                   h->cfg.t0, h->pers_dir, h->stream));
+    h->launches += 4;
+    return CPM_OK;
+}
+
 int run_subpass(cpm_handle *h)
 {
     if (h->act && h->sp == 0 && h->t % 64 == 0) {
@@ -221,6 +258,8 @@ int run_subpass(cpm_handle *h)
     a.key0 = (uint32_t)h->cfg.seed;
     a.key1 = (uint32_t)(h->cfg.seed >> 32);
     a.tp = h->tp;
+    a.chem = h->chem;
+    a.pers_dir = h->pers ? h->pers_dir : nullptr;
     pick_bricks(h->dim, a.nax, a.nay, a);
     for (uint32_t r = 0; r < h->k; r++) {
         const int cur = (int)(h->g & 1);
@@ -239,6 +278,7 @@ int run_subpass(cpm_handle *h)
     if (++h->sp == (int32_t)h->per_mcs) {
         h->sp = 0;
         h->t += 1;
+        if (h->pers) return pers_step(h);
     }
     return CPM_OK;
 }
@@ -450,6 +490,12 @@ void free_all(cpm_handle *h)
         cudaFree(h->ln_tab);
         cudaFree(h->expq);
     }
+    cudaFree(h->chem);
+    cudaFree(h->pers_dir);
+    cudaFree(h->pers_hist);
+    cudaFree(h->pers_item);
+    cudaFree(h->pers_cells);
+    cudaFree(h->pers_member);
     cudaFree(h->counters);
     cudaFree(h->act_tmp);
     cudaFree(h->error_flag);
@@ -487,6 +533,10 @@ int create_impl(cpm_handle *h, const cpm_config *c, TableCache *cache = nullptr)
     memcpy(h->tp.lambda_act, c->lambda_act, sizeof h->tp.lambda_act);
     memcpy(h->tp.max_act, c->max_act, sizeof h->tp.max_act);
     h->tp.obstacle_type = c->obstacle_type;
+    memcpy(h->tp.lambda_chem, c->lambda_chem, sizeof h->tp.lambda_chem);
+    memcpy(h->tp.lambda_pers, c->lambda_pers, sizeof h->tp.lambda_pers);
+    for (int k = 0; k < 4; k++) h->tp.inv_len[k] = k ? 1.0 / std::sqrt((double)k) : 0.0;
+    h->cfg.chem_field = nullptr;
     for (int a = 0; a < CPM_MAX_TYPES; a++) {
         if (c->lambda_p[a]) h->perim = true;
         if (c->lambda_act[a]) h->act = true;
@@ -532,6 +582,43 @@ int create_impl(cpm_handle *h, const cpm_config *c, TableCache *cache = nullptr)
     if (rc) return rc;
     rc = reset_tallies(h);
     if (rc) return rc;
+    if (c->chem_field) {
+        const size_t bytes = sizeof(int16_t) * (size_t)h->n_sites * (size_t)c->dim;
+        CUDA_TRY(h, cudaMalloc(&h->chem, bytes));
+        CUDA_TRY(h, cudaMemcpyAsync(h->chem, c->chem_field, bytes, cudaMemcpyHostToDevice, h->stream));
+    }
+    for (int a = 0; a < CPM_MAX_TYPES; a++) {
+        h->pp.lambda[a] = c->lambda_pers[a];
+        h->pp.dt[a] = c->dt_pers[a];
+        h->pp.mu[a] = c->mu_pers[a];
+        if (c->lambda_pers[a] != 0) {
+            h->pers = true;
+            h->pers_H = std::max<int32_t>(h->pers_H, c->dt_pers[a] + 1);
+        }
+    }
+    if (h->pers) {
+        const size_t nc = (size_t)h->n_cells + 1;
+        CUDA_TRY(h, cudaMalloc(&h->pers_dir, sizeof(double) * 3 * nc));
+        CUDA_TRY(h, cudaMalloc(&h->pers_hist, sizeof(double) * 3 * nc * (size_t)h->pers_H));
+        CUDA_TRY(h, cudaMalloc(&h->pers_item, sizeof(ObserveItem)));
+        CUDA_TRY(h, cudaMalloc(&h->pers_cells, sizeof(int64_t) * kObsFields * nc));
+        CUDA_TRY(h, cudaMalloc(&h->pers_member, sizeof(int64_t) * 2));
+        CUDA_TRY(h, cudaMemsetAsync(h->pers_dir, 0, sizeof(double) * 3 * nc, h->stream));
+        // all-ones bytes are a NaN: no centroid recorded yet
+        CUDA_TRY(h, cudaMemsetAsync(h->pers_hist, 0xFF, sizeof(double) * 3 * nc * (size_t)h->pers_H, h->stream));
+        ObserveItem it{};
+        it.lat = h->lat;
+        it.accepts = h->counters;
+        it.nx = (uint32_t)c->nx;
+        it.ny = (uint32_t)c->ny;
+        it.nz = (uint32_t)(c->dim == 3 ? c->nz : 1);
+        it.dim = (uint32_t)c->dim;
+        it.row0 = 0;
+        it.n_cells = h->n_cells;
+        CUDA_TRY(h, cudaMemcpyAsync(h->pers_item, &it, sizeof it, cudaMemcpyHostToDevice, h->stream));
+        rc = pers_step(h);  // the centroids at t0: the first look-back point
+        if (rc) return rc;
+    }
     if (!cache) CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return CPM_OK;
 }
@@ -620,6 +707,20 @@ int cpm_read_tallies(cpm_handle *h, int32_t *V, int32_t *A, int dst_is_device)
     const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (V) CUDA_TRY(h, cudaMemcpyAsync(V, V_buf(h, cur), bytes, kind, h->stream));
     if (A) CUDA_TRY(h, cudaMemcpyAsync(A, A_buf(h, cur), bytes, kind, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return CPM_OK;
+}
+
+int cpm_read_persistence(cpm_handle *h, double *dir)
+{
+    if (bad(h)) return CPM_E_HANDLE;
+    if (!dir) return fail(h, CPM_E_INVALID, "dir is NULL");
+    const size_t n = 3 * ((size_t)h->n_cells + 1);
+    if (!h->pers) {
+        memset(dir, 0, sizeof(double) * n);
+        return CPM_OK;
+    }
+    CUDA_TRY(h, cudaMemcpyAsync(dir, h->pers_dir, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return CPM_OK;
 }
@@ -908,6 +1009,14 @@ int cpm_batch_create(const cpm_config *cfgs, int32_t n, void *cuda_stream, cpm_b
         for (auto &th : pool) th.join();
     }
     for (int32_t i = 0; i < n; i++) {
+        bool pers = false;
+        for (int a = 0; a < CPM_MAX_TYPES; a++) pers |= cfgs[i].lambda_pers[a] != 0;
+        if (pers) {
+            batch_free(b);
+            delete b;
+            return bfail(nullptr, CPM_E_INVALID, "configuration " + std::to_string(i) +
+                                                     ": the persistence term needs single-lattice handles");
+        }
         if (cfgs[i].dim != b->dim || cfgs[i].tile != 0) {
             batch_free(b);
             delete b;
@@ -945,6 +1054,7 @@ int cpm_batch_create(const cpm_config *cfgs, int32_t n, void *cuda_stream, cpm_b
         a.key0 = (uint32_t)h->cfg.seed;
         a.key1 = (uint32_t)(h->cfg.seed >> 32);
         a.tp = h->tp;
+        a.chem = h->chem;
         for (int p = 0; p < 2; p++) {
             L.V[p] = V_buf(h, p);
             L.A[p] = A_buf(h, p);

@@ -63,6 +63,8 @@ struct TypeParams {
     int32_t lambda_p[kMaxTypes], a_target[kMaxTypes];
     int32_t lambda_act[kMaxTypes], max_act[kMaxTypes];
     int32_t obstacle_type;
+    int32_t lambda_chem[kMaxTypes], lambda_pers[kMaxTypes];  // motility weights, scaled
+    double inv_len[4];                                        // 1 / sqrt(k), k = |d|^2 of a copy direction
 };
 
 // Everything one round of the sweep needs.
@@ -88,6 +90,8 @@ struct RoundArgs {
     uint32_t t, sp, r;         // MCS (low 32 bits), sub-pass, round
     uint32_t key0, key1;
     uint32_t brick_x, brick_y, brick_z;  // active blocks per CTA along each axis (product <= 256)
+    const int16_t *chem;       // chemotaxis field, dim int16 per site (Q14), or null
+    const double *pers_dir;    // persistence directions, 3 per cell id, or null
     TypeParams tp;
 };
 
@@ -121,6 +125,15 @@ struct ObserveItem {
 };
 cudaError_t launch_observe(int dim, const ObserveItem *d_items, uint32_t n_items, int64_t max_sites, int64_t *cells,
                            int64_t *member, cudaStream_t st);
+
+// Persistence update at the end of an MCS (Eq. 6, Eq. 7) from one observation of the lattice.
+struct PersParams {
+    int32_t lambda[kMaxTypes], dt[kMaxTypes];
+    double mu[kMaxTypes];
+};
+cudaError_t launch_pers_update(const int64_t *cells, int32_t n_cells, uint32_t nx, uint32_t ny, uint32_t nz,
+                               const uint8_t *cell_type, const PersParams &pp, double *hist, int32_t H, int64_t t,
+                               int64_t t0, double *dir, cudaStream_t st);
 
 // Summary statistics of 2D lattices from a stack of observations (cpm_batch_summarize).
 constexpr int kSummaryStats = 16;

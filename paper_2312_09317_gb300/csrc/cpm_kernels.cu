@@ -107,6 +107,40 @@ __device__ __forceinline__ int64_t floor_div_pos(int64_t num, int64_t den)
     return q;
 }
 
+// Motility terms (Eq. 4, Eq. 5) of the copy from the source (stencil index
+// ox, oy, oz around the target) into the target, in 1/16 energy units: the
+// moving cell is si (sj when si is the medium), d = target - source, and
+// each term is floor(e) with e formed by the same rounded double operations,
+// in the same order, as the replay: chemotaxis
+// e = ((double)(-16 lambda (d . C_q)) / 16384) * (1/|d|), persistence
+// e = ((d_x p_x + d_y p_y + d_z p_z) * (double)(-16 lambda)) * (1/|d|).
+template <int DIM>
+__device__ __forceinline__ int64_t motility_q(const RoundArgs &a, int32_t si, int32_t sj, int ti, int tj, int ox,
+                                              int oy, int oz, uint32_t isite)
+{
+    const int32_t m = si > 0 ? si : sj;
+    const int tp = si > 0 ? ti : tj;
+    const int dx = 1 - ox, dy = 1 - oy, dz = DIM == 3 ? 1 - oz : 0;
+    const double il = a.tp.inv_len[dx * dx + dy * dy + dz * dz];
+    int64_t dh = 0;
+    if (a.chem && a.tp.lambda_chem[tp] != 0) {
+        const int16_t *c = a.chem + (size_t)isite * DIM;
+        int64_t dc = (int64_t)dx * c[0] + (int64_t)dy * c[1];
+        if (DIM == 3) dc += (int64_t)dz * c[2];
+        const double e = __dmul_rn((double)(-16 * (int64_t)a.tp.lambda_chem[tp] * dc) / 16384.0, il);
+        dh += (int64_t)floor(e);
+    }
+    if (a.pers_dir && a.tp.lambda_pers[tp] != 0 && m > 0) {
+        const double *ph = a.pers_dir + 3 * (size_t)m;
+        double sd = __dmul_rn((double)dx, ph[0]);
+        sd = __dadd_rn(sd, __dmul_rn((double)dy, ph[1]));
+        sd = __dadd_rn(sd, __dmul_rn((double)dz, ph[2]));
+        const double e = __dmul_rn(__dmul_rn(sd, (double)(-16 * (int64_t)a.tp.lambda_pers[tp])), il);
+        dh += (int64_t)floor(e);
+    }
+    return dh;
+}
+
 // One copy attempt of active block (ix, iy, iz) (active index i) in the round
 // described by a; also carries the previous round's change of index i into
 // the next tallies.  Returns whether the copy was accepted.
@@ -196,6 +230,7 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
                         dhq += floor_div_pos(lam * (gj - gi), mx * 4096);
                     }
                 }
+                if (a.chem || a.pers_dir) dhq += motility_q<DIM>(a, si, sj, ti, tj, ox, oy, oz, isite);
                 const bool ok = dhq <= 0 || (dhq < a.L && w.v[2] < __ldg(a.thr + dhq));
                 if (ok) {
                     a.lat[j] = si;

@@ -111,6 +111,9 @@ extern "C" int cpm_step_noalloc(const cpm_config *cfg, int32_t *lattice, int32_t
         return na_fail(CPM_E_INVALID, "bad position or count");
     if (!(c.temperature > 0.0)) return na_fail(CPM_E_INVALID, "temperature must be > 0");
     if (c.tile != 0) return na_fail(CPM_E_INVALID, "only the global schedule (tile = 0) runs here");
+    bool motility = c.chem_field != nullptr;
+    for (int a = 0; a < CPM_MAX_TYPES; a++) motility |= c.lambda_chem[a] != 0 || c.lambda_pers[a] != 0;
+    if (motility) return na_fail(CPM_E_INVALID, "no motility terms here");
 
     // integer tables, on the stack
     uint32_t thr[kNaMaxThr];

@@ -337,7 +337,72 @@ __global__ void __launch_bounds__(kSumThreads) summarize_kernel(const ObserveIte
     if (acc[A_EL + 1] > 0.0) o[15] = acc[A_EL] / acc[A_EL + 1];
 }
 
+// Persistence update (Eq. 6, Eq. 7) for every cell, one thread per cell,
+// from this MCS's observation rows: record the centroid (anchor + offset
+// sums / volume, NaN for an absent cell) in history slot t % H, then blend
+// the unit displacement over dt MCS into p_hat.  Every operation is a single
+// rounded double operation in the order the replay uses (no contraction).
+__global__ void pers_update_kernel(const int64_t *cells, int32_t n_cells, uint32_t nx, uint32_t ny, uint32_t nz,
+                                   const uint8_t *cell_type, const PersParams pp, double *hist, int32_t H,
+                                   int64_t t, int64_t t0, double *dir)
+{
+    const int64_t c = 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > n_cells) return;
+    const int64_t nc = (int64_t)n_cells + 1;
+    const int64_t *r = cells + c * kObsFields;
+    double *Xn = hist + 3 * (nc * (t % H) + c);
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+    if (r[1] <= 0) {
+        Xn[0] = Xn[1] = Xn[2] = qnan;
+        return;
+    }
+    const int64_t an = r[0], plane = (int64_t)nx * ny;
+    const double V = (double)r[1];
+    const double ac[3] = {(double)(an % nx), (double)((an / nx) % ny), (double)(an / plane)};
+    for (int d = 0; d < 3; ++d) Xn[d] = __dadd_rn(ac[d], __ddiv_rn((double)r[2 + d], V));
+    const int tp = cell_type[c];
+    const int dt = pp.dt[tp];
+    if (pp.lambda[tp] == 0 || dt < 1 || t - dt < t0) return;
+    const double *Xo = hist + 3 * (nc * ((t - dt) % H) + c);
+    if (isnan(Xo[0])) return;
+    const double L[3] = {(double)nx, (double)ny, (double)nz};
+    double D[3];
+    for (int d = 0; d < 3; ++d) {
+        const double v = __dsub_rn(Xn[d], Xo[d]);
+        D[d] = __dsub_rn(v, __dmul_rn(L[d], rint(__ddiv_rn(v, L[d]))));
+    }
+    double n2 = __dmul_rn(D[0], D[0]);
+    n2 = __dadd_rn(n2, __dmul_rn(D[1], D[1]));
+    n2 = __dadd_rn(n2, __dmul_rn(D[2], D[2]));
+    if (n2 == 0.0) return;
+    const double n = __dsqrt_rn(n2), mu = pp.mu[tp], am = __dsub_rn(1.0, mu);
+    double *ph = dir + 3 * c, q[3];
+    for (int d = 0; d < 3; ++d) {
+        const double u = __ddiv_rn(D[d], n);
+        q[d] = __dadd_rn(__dmul_rn(am, u), __dmul_rn(mu, ph[d]));
+    }
+    double m2 = __dmul_rn(q[0], q[0]);
+    m2 = __dadd_rn(m2, __dmul_rn(q[1], q[1]));
+    m2 = __dadd_rn(m2, __dmul_rn(q[2], q[2]));
+    if (m2 == 0.0) {
+        ph[0] = ph[1] = ph[2] = 0.0;
+        return;
+    }
+    const double m = __dsqrt_rn(m2);
+    for (int d = 0; d < 3; ++d) ph[d] = __ddiv_rn(q[d], m);
+}
+
 }  // namespace
+
+cudaError_t launch_pers_update(const int64_t *cells, int32_t n_cells, uint32_t nx, uint32_t ny, uint32_t nz,
+                               const uint8_t *cell_type, const PersParams &pp, double *hist, int32_t H, int64_t t,
+                               int64_t t0, double *dir, cudaStream_t st)
+{
+    if (n_cells < 1) return cudaSuccess;
+    pers_update_kernel<<<(n_cells + 127) / 128, 128, 0, st>>>(cells, n_cells, nx, ny, nz, cell_type, pp, hist, H, t,
+                                                              t0, dir);
+    return cudaPeekAtLastError();
+}
 
 cudaError_t launch_summarize(const ObserveItem *d_items, uint32_t n_items, int32_t max_cells, const int64_t *cells,
                              int64_t rows, const int64_t *member, int32_t n_snap, int32_t every, double *traj,

@@ -109,3 +109,16 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.cpm_read_lattice(None, None, 0) == cpm.CPM_E_HANDLE
     assert lib.cpm_kernel_launches(None) == 0
     lib.cpm_destroy(None)
+
+
+def test_motility_settings_are_checked_without_a_gpu(lib):
+    w = cw.random_small(3, dim=2, n=32, n_cells=4, a=4, c=2, P=4)
+    wc = cw.with_motility(w, chem=cw.uniform_field((1, 32, 32), 2, (1, 0)), lambda_chem=5)
+    rc, err = _create(wc.replace(tile=8, tile_cycles=1))
+    assert rc == cpm.CPM_E_INVALID and "global schedule" in err
+    wp = cw.with_motility(w, lambda_pers=5, mu=0.5, dt=0)
+    rc, err = _create(wp)
+    assert rc == cpm.CPM_E_INVALID and "dt_pers" in err
+    wp = cw.with_motility(w, lambda_pers=5, mu=1.5, dt=2)
+    rc, err = _create(wp)
+    assert rc == cpm.CPM_E_INVALID and "mu_pers" in err
