@@ -674,7 +674,8 @@ def run_emulator_sweep(args):
             },
             "roofline": {"bound": "tensor", "achieved": tflops, "peak": pk[0], "unit": "TFLOP/s",
                          "frac": tflops / pk[0], "traffic": None, "peak_kind": "of %s" % pk[1],
-                         "kernel": "gemm_kernel (emulator inference, 1M points, mma.sync bf16)",
+                         "kernel": "gemm_tc_kernel (tcgen05, TMEM accumulators) over the 1M-point prediction: "
+                                   "every forward layer, the gathers and the ensemble/fallback kernel",
                          "inference_points_per_s": Xi.shape[0] / inf_s},
             "cpu_baseline": None,
             "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": block * 7 * 4,

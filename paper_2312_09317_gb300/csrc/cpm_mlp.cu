@@ -324,10 +324,10 @@ __global__ void predict_kernel(int rows, int n_members, int n_out, const float *
 // matrices 128 B apart (leading byte offset), 8-row groups Kp/8 x 128 B apart
 // (stride byte offset).  One thread issues Kp/16 tcgen05.mma (bf16 x bf16 ->
 // f32, M = 128, N <= 256) into a TMEM accumulator and commits them to an
-// mbarrier; after a bounded wait the eight warps read the accumulator with
-// tcgen05.ld (warp w owns TMEM lanes 32 (w % 4) .. + 31 and every other
+// mbarrier; after a bounded wait the sixteen warps read the accumulator with
+// tcgen05.ld (warp w owns TMEM lanes 32 (w % 4) .. + 31 and every fourth
 // 16-column chunk) and apply the bias / GELU epilogue.
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;  // 16 warps: each TMEM lane quarter is read by 4 warps
 constexpr int kTcM = 128;
 constexpr uint32_t kTcSpinLimit = 1u << 22;
 constexpr int kTcNotApplicable = 1;  // launch_gemm_tc: use the mma.sync kernel instead
@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const TcArgs p)
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(p.N >> 3) << 17) |
                            ((uint32_t)(kTcM >> 4) << 24);
     const uint32_t sbo = (uint32_t)(p.Kp / 8) * 128u;
-    const int q = warp & 3, half = warp >> 2, nchunk = p.N / 16;
+    const int q = warp & 3, part = warp >> 2, nparts = kTcThreads / 128, nchunk = p.N / 16;
     int cur_z = -1;
     uint32_t phase = 0;
     bool aborted = false;
@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const TcArgs p)
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int row = m0 + q * 32 + lane;
-        for (int ch = half; ch < nchunk; ch += 2) {
+        for (int ch = part; ch < nchunk; ch += nparts) {
             uint32_t r[16];
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ch * 16);
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
