@@ -580,6 +580,14 @@ int create_impl(cpm_handle *h, const cpm_config *c, TableCache *cache = nullptr)
     }
     int rc = cache ? build_tables_cached(h, cache) : build_tables(h);
     if (rc) return rc;
+    {
+        std::vector<int32_t> ln, ex;
+        ln_expq_tables(ln, ex);
+        for (int a = 0; a < CPM_MAX_TYPES; a++) {
+            const int m = c->max_act[a] < 0 ? 0 : (c->max_act[a] > 127 ? 127 : c->max_act[a]);
+            h->tp.gm_max[a] = m > 0 ? ex[ln[m] >> 6] : 0;
+        }
+    }
     rc = reset_tallies(h);
     if (rc) return rc;
     if (c->chem_field) {

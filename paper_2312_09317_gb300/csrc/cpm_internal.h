@@ -65,6 +65,7 @@ struct TypeParams {
     int32_t obstacle_type;
     int32_t lambda_chem[kMaxTypes], lambda_pers[kMaxTypes];  // motility weights, scaled
     double inv_len[4];                                        // 1 / sqrt(k), k = |d|^2 of a copy direction
+    int32_t gm_max[kMaxTypes];  // EXPQ[LN[Max_act] >> 6]: the largest Act geometric mean a type's site can have
 };
 
 // Everything one round of the sweep needs.

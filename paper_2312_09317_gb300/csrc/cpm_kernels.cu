@@ -220,18 +220,29 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
                     }
                 }
                 int64_t dhq = 16 * dh;
+                if (a.chem || a.pers_dir) dhq += motility_q<DIM>(a, si, sj, ti, tj, ox, oy, oz, isite);
+                // decided: 1 accept, 0 reject, -1 open
+                int decided = -1;
                 if (ACT) {
                     const int tp = si > 0 ? ti : tj;
                     const int64_t lam = sm.la[tp], mx = sm.ma[tp];
                     if (lam != 0 && mx != 0) {
-                        const uint32_t ix_ = xs[ox], iy_ = ys[oy], iz_ = zs[oz];
-                        const int64_t gi = gm_q<DIM>(a, sm, ix_, iy_, iz_, si, si > 0 ? sm.ma[ti] : 0);
-                        const int64_t gj = gm_q<DIM>(a, sm, jx, jy, jz, sj, sj > 0 ? sm.ma[tj] : 0);
-                        dhq += floor_div_pos(lam * (gj - gi), mx * 4096);
+                        // the Act term lies in [floor(-lam Gmax_i / (Max 4096)), floor(lam Gmax_j / (Max 4096))]
+                        // (GM in [0, Gmax] per cell, lambda >= 0); when every value in that range gives the same
+                        // outcome of the test below (THR is non-increasing), the geometric means are not needed
+                        const int64_t lo = dhq + floor_div_pos(-lam * (si > 0 ? a.tp.gm_max[ti] : 0), mx * 4096);
+                        const int64_t hi = dhq + floor_div_pos(lam * (sj > 0 ? a.tp.gm_max[tj] : 0), mx * 4096);
+                        if (hi <= 0) decided = 1;
+                        else if (lo >= a.L || (lo > 0 && w.v[2] >= __ldg(a.thr + lo))) decided = 0;
+                        else {
+                            const uint32_t ix_ = xs[ox], iy_ = ys[oy], iz_ = zs[oz];
+                            const int64_t gi = gm_q<DIM>(a, sm, ix_, iy_, iz_, si, si > 0 ? sm.ma[ti] : 0);
+                            const int64_t gj = gm_q<DIM>(a, sm, jx, jy, jz, sj, sj > 0 ? sm.ma[tj] : 0);
+                            dhq += floor_div_pos(lam * (gj - gi), mx * 4096);
+                        }
                     }
                 }
-                if (a.chem || a.pers_dir) dhq += motility_q<DIM>(a, si, sj, ti, tj, ox, oy, oz, isite);
-                const bool ok = dhq <= 0 || (dhq < a.L && w.v[2] < __ldg(a.thr + dhq));
+                const bool ok = decided >= 0 ? decided == 1 : (dhq <= 0 || (dhq < a.L && w.v[2] < __ldg(a.thr + dhq)));
                 if (ok) {
                     a.lat[j] = si;
                     if (ACT && a.stamp) a.stamp[j] = (uint8_t)(si > 0 ? (a.t & 255u) : ((a.t - 128u) & 255u));
