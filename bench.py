@@ -100,11 +100,12 @@ DEFAULT_WORKLOAD = "cpm3d_tissue_1024"
 # DRAM bytes per round-kernel launch from the last ncu capture, valid only for
 # the kernel source it was taken on (sha1 of csrc/cpm_kernels.cu, first 12 hex).
 # The 1024^3 tissue launch is too large to capture; its figure is the 512^3
-# capture (503.8 MB read + 65.2 MB written per launch) scaled by the 8x sites:
-# one round streams the lattice once, so traffic grows with the sites.
+# capture after the growth burn-in (498.0 MB read + 38.4 MB written per launch)
+# scaled by the 8x sites: one round streams the lattice once, so traffic grows
+# with the sites.
 NCU_TRAFFIC = {
-    ("cpm3d_tissue_1024", "d49ef2000078"): 8 * (503.849216e6 + 65.235456e6),
-    ("cpm3d_tissue_512", "d49ef2000078"): 503.849216e6 + 65.235456e6,
+    ("cpm3d_tissue_1024", "86ff13bdf341"): 8 * (498.015488e6 + 38.370304e6),
+    ("cpm3d_tissue_512", "86ff13bdf341"): 498.015488e6 + 38.370304e6,
 }
 
 
