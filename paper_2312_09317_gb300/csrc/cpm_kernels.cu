@@ -257,14 +257,21 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
     return accepted;
 }
 
-// Four resident CTAs per SM (at most 64 registers a thread): the round kernel
-// is latency-bound, and the Act variant gains ~40% over 128 registers.
+// Resident CTAs per SM (register budget): the round kernel is latency-bound.
+// Measured on GB300 in same-box A/B runs: without Act, four CTAs of 256
+// (64 registers) are fastest (config 2: 1.05 ms per MCS against 1.31 at 32
+// registers); with Act, eight (32 registers, a few spills) are fastest
+// (1024^3 tissue: 147 ms per MCS against 173 at 64 registers).
 #ifndef CPM_ROUND_MIN_BLOCKS
 #define CPM_ROUND_MIN_BLOCKS 4
 #endif
+#ifndef CPM_ROUND_MIN_BLOCKS_ACT
+#define CPM_ROUND_MIN_BLOCKS_ACT 8
+#endif
 
 template <int DIM, bool PERIM, bool ACT>
-__global__ void __launch_bounds__(kThreads, CPM_ROUND_MIN_BLOCKS) round_kernel(const RoundArgs a)
+__global__ void __launch_bounds__(kThreads, ACT ? CPM_ROUND_MIN_BLOCKS_ACT : CPM_ROUND_MIN_BLOCKS)
+    round_kernel(const RoundArgs a)
 {
     __shared__ SmemTables sm;
     load_tables(sm, a, ACT);
@@ -293,8 +300,17 @@ __global__ void __launch_bounds__(kThreads, CPM_ROUND_MIN_BLOCKS) round_kernel(c
 // Batched round: every CTA takes one (lattice, chunk of 128 active blocks)
 // item and runs that lattice's round number g_start + q, exactly as the
 // single-lattice round kernel would (same colour, counters and tallies).
+// Register budget of the batched round as for round_kernel: with Act eight
+// CTAs of 256 per SM (the 512-member ensemble: 31.2 ms per MCS against 36.7
+// at two CTAs), without Act four.
+#ifndef CPM_BATCH_MIN_BLOCKS
+#define CPM_BATCH_MIN_BLOCKS 4
+#endif
+#ifndef CPM_BATCH_MIN_BLOCKS_ACT
+#define CPM_BATCH_MIN_BLOCKS_ACT 8
+#endif
 template <int DIM, bool PERIM, bool ACT>
-__global__ void __launch_bounds__(kBatchMaxThreads, 2)
+__global__ void __launch_bounds__(kBatchMaxThreads, ACT ? CPM_BATCH_MIN_BLOCKS_ACT : CPM_BATCH_MIN_BLOCKS)
     batch_round_kernel(const BatchLattice *lats, const int2 *items, uint32_t q)
 {
     __shared__ RoundArgs ra;
