@@ -100,12 +100,12 @@ DEFAULT_WORKLOAD = "cpm3d_tissue_1024"
 # DRAM bytes per round-kernel launch from the last ncu capture, valid only for
 # the kernel source it was taken on (sha1 of csrc/cpm_kernels.cu, first 12 hex).
 # The 1024^3 tissue launch is too large to capture; its figure is the 512^3
-# capture after the growth burn-in (498.0 MB read + 38.4 MB written per launch)
+# capture after the growth burn-in (553.2 MB read + 167.6 MB written per launch)
 # scaled by the 8x sites: one round streams the lattice once, so traffic grows
 # with the sites.
 NCU_TRAFFIC = {
-    ("cpm3d_tissue_1024", "86ff13bdf341"): 8 * (498.015488e6 + 38.370304e6),
-    ("cpm3d_tissue_512", "86ff13bdf341"): 498.015488e6 + 38.370304e6,
+    ("cpm3d_tissue_1024", "493ce79f74ee"): 8 * (553.170944e6 + 167.580416e6),
+    ("cpm3d_tissue_512", "493ce79f74ee"): 553.170944e6 + 167.580416e6,
 }
 
 
