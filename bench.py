@@ -449,7 +449,8 @@ def run_gpu(args):
         try:
             import argparse as _ap
             sa = _ap.Namespace(**vars(args))
-            sa.workload, sa.steps, sa.warmup = "emulator_sweep", 3, 3
+            # a quarter-million-point block per step keeps the default run within minutes
+            sa.workload, sa.steps, sa.warmup, sa.emu_block = "emulator_sweep", 2, 1, 1 << 18
             torch.cuda.empty_cache()
             sl = emulator_sweep_measure(sa, 0, 1, None)
             line["sweep"] = {"metric": sl["metric"], "value": sl["value"], "unit": sl["unit"],
@@ -667,7 +668,7 @@ def emulator_sweep_measure(args, rank=0, ws_=1, dist=None):
             tm_sweep = {}
             lib_l0 = emu.net.launches()
         t0 = time.perf_counter()
-        Ys, f = emu.sweep(Xs, seed=seed0 + 2000 + k, replicates=r_star, timings=tm_sweep, **sim)
+        Ys, f = emu.sweep(Xs, seed=seed0 + 2000 + k, replicates=r_star, timings=tm_sweep, chunk=8192, **sim)
         torch.cuda.synchronize()
         if k >= args.warmup:
             times.append(time.perf_counter() - t0)
@@ -760,7 +761,7 @@ def main():
                     choices=sorted(WORKLOADS) + sorted(ENSEMBLES) + sorted(EMULATOR))
     ap.add_argument("--emu-runs", type=int, default=100000, help="training runs of the emulator")
     ap.add_argument("--emu-eval", type=int, default=256, help="held-out points with replicate truth")
-    ap.add_argument("--emu-block", type=int, default=4096, help="query points per sweep step")
+    ap.add_argument("--emu-block", type=int, default=1 << 20, help="query points per sweep step (config 5: 1M)")
     ap.add_argument("--no-sweep", action="store_true", help="default workload: skip the embedded emulator sweep")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
