@@ -21,6 +21,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -37,39 +38,39 @@ UNIT = "attempts/s"
 # Workloads: (factory, algorithmic bytes per site per MCS, description)
 # bytes: int32 lattice read + write (8 B); with Act the uint8 stamp read + write (2 B).
 WORKLOADS = {
-    "cpm2d_200": (lambda: cw.config1_2d(seed=1), 8,
+    "cpm2d_200": (lambda: cw.point_cells_2d(seed=1), 8,
                   "2D 200x200 Moore-8, 100 one-pixel cells, V_t=100, J(c,c)=20, J(c,m)=10, lambda_V=50, T=20; "
                   "a=4, c=2, P=1"),
-    "cpm3d_256": (lambda: cw.config2_3d(seed=1, n=256, a=4, c=2, P=8), 8,
+    "cpm3d_256": (lambda: cw.cube_cells_3d(seed=1, n=256, a=4, c=2, P=8), 8,
                   "3D 256^3 Moore-26, ~17,576 cells, V_t=500, A_t=400, lambda_V=25, lambda_P=0.5, "
                   "J(c,c)=20, J(c,m)=12, T=20 (x2 integer scale); a=4, c=2, P=8"),
     # the same model on a lattice larger than L2, for DRAM counters
-    "cpm3d_512": (lambda: cw.config2_3d(seed=1, n=512, a=4, c=2, P=8), 8,
+    "cpm3d_512": (lambda: cw.cube_cells_3d(seed=1, n=512, a=4, c=2, P=8), 8,
                   "3D 512^3, otherwise as cpm3d_256"),
-    "cpm3d_tissue_1024": (lambda: cw.config3_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda"), 10,
+    "cpm3d_tissue_1024": (lambda: cw.fibre_tissue_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda"), 10,
                           "3D tissue 1024^3 Moore-26 with a Voronoi-edge fibre mask (15% frozen), ~0.9M motile "
                           "cells, V_t=800, A_t=4639, Act lambda=200 Max=30, J(c,c)=20, J(c,m)=10, "
                           "J(c,fibre)=40, lambda_V=25, lambda_P=0.2, T=20 (x5 integer scale); a=4, c=2, P=8"),
-    "cpm3d_tissue_512": (lambda: cw.config3_3d(seed=1, n=512, a=4, c=2, P=8, device="cuda"), 10,
+    "cpm3d_tissue_512": (lambda: cw.fibre_tissue_3d(seed=1, n=512, a=4, c=2, P=8, device="cuda"), 10,
                          "3D tissue 512^3, otherwise as cpm3d_tissue_1024"),
     # the tissue workload under the tiled schedule (tiles of edge 16, one tile cycle per MCS)
-    "cpm3d_tissue_1024_tiled": (lambda: cw.config3_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda")
+    "cpm3d_tissue_1024_tiled": (lambda: cw.fibre_tissue_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda")
                                 .replace(tile=16, tile_cycles=1), 10,
                                 "as cpm3d_tissue_1024, tiled schedule: tiles of edge 16, 1 tile cycle per MCS"),
-    "cpm3d_tissue_1024_tiled2": (lambda: cw.config3_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda")
+    "cpm3d_tissue_1024_tiled2": (lambda: cw.fibre_tissue_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda")
                                  .replace(tile=16, tile_cycles=2), 10,
                                  "as cpm3d_tissue_1024, tiled schedule: tiles of edge 16, 2 tile cycles per MCS"),
-    "cpm3d_tissue_1024_t32p8": (lambda: cw.config3_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda")
+    "cpm3d_tissue_1024_t32p8": (lambda: cw.fibre_tissue_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda")
                                 .replace(tile=32, tile_cycles=8), 10,
                                 "as cpm3d_tissue_1024, tiled schedule: tiles of edge 32, 8 tile cycles per MCS"),
-    "cpm3d_tissue_512_t32p8": (lambda: cw.config3_3d(seed=1, n=512, a=4, c=2, P=8, device="cuda")
+    "cpm3d_tissue_512_t32p8": (lambda: cw.fibre_tissue_3d(seed=1, n=512, a=4, c=2, P=8, device="cuda")
                                .replace(tile=32, tile_cycles=8), 10,
                                "3D tissue 512^3, tiled schedule: tiles of edge 32, 8 tile cycles per MCS"),
-    "cpm3d_tissue_512_tiled": (lambda: cw.config3_3d(seed=1, n=512, a=4, c=2, P=8, device="cuda")
+    "cpm3d_tissue_512_tiled": (lambda: cw.fibre_tissue_3d(seed=1, n=512, a=4, c=2, P=8, device="cuda")
                                .replace(tile=16, tile_cycles=1), 10,
                                "3D tissue 512^3, tiled schedule: tiles of edge 16"),
 }
-# Ensembles (config 4): many independent lattices of uneven sizes advanced
+# Ensembles for parameter sweeps: many independent lattices of uneven sizes advanced
 # together; a step is one MCS of every member.
 ENSEMBLES = {
     "cpm_ensemble_512": (lambda: cw.ensemble(512, seed=1),
@@ -79,7 +80,7 @@ ENSEMBLES = {
                          "batches on one stream"),
 }
 
-# The emulator (config 5): sweep points answered at <= 5% error on the summary
+# The emulator of the parameter sweep: sweep points answered at <= 5% error on the summary
 # statistics, emulator + CPM fallback against the CPM alone.
 EMULATOR = {
     "emulator_sweep": "MLP-ensemble emulator (5 x 7-256x4-16, GELU, bf16/fp32) of 16 summary statistics of 2D "
@@ -100,12 +101,12 @@ DEFAULT_WORKLOAD = "cpm3d_tissue_1024"
 # DRAM bytes per round-kernel launch from the last ncu capture, valid only for
 # the kernel source it was taken on (sha1 of csrc/cpm_kernels.cu, first 12 hex).
 # The 1024^3 tissue launch is too large to capture; its figure is the 512^3
-# capture after the growth burn-in (553.2 MB read + 167.6 MB written per launch)
+# capture after the growth burn-in (539.0 MB read + 145.0 MB written per launch)
 # scaled by the 8x sites: one round streams the lattice once, so traffic grows
 # with the sites.
 NCU_TRAFFIC = {
-    ("cpm3d_tissue_1024", "493ce79f74ee"): 8 * (553.170944e6 + 167.580416e6),
-    ("cpm3d_tissue_512", "493ce79f74ee"): 553.170944e6 + 167.580416e6,
+    ("cpm3d_tissue_1024", "8b126a6442c7"): 8 * (539.005184e6 + 144.968448e6),
+    ("cpm3d_tissue_512", "8b126a6442c7"): 539.005184e6 + 144.968448e6,
 }
 
 
@@ -139,10 +140,11 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, path: str | None = None):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+        # the raw samples: a file the caller names (--clocks-csv), else a temporary one
+        self.path = path or os.path.join(tempfile.gettempdir(), "clocks_bench_%d.csv" % os.getpid())
 
     def start(self):
         try:
@@ -355,7 +357,7 @@ def run_gpu(args):
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     l0 = sim.launches()
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clocks_csv)
     clocks.start()
     barrier(dist)
     torch.cuda.synchronize()
@@ -508,7 +510,7 @@ def run_gpu_batch(args):
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     l0 = sum(b.launches() for b in batches)
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clocks_csv)
     clocks.start()
     barrier(dist)
     torch.cuda.synchronize()
@@ -601,7 +603,7 @@ def run_gpu_batch(args):
 
 
 def run_emulator_sweep(args):
-    """Config 5: train the emulator on batched-CPM runs, measure its error
+    """Emulator sweep: train the emulator on batched-CPM runs, measure its error
     against replicate means of the CPM at held-out points, then time sweeps
     answered by emulator + CPM fallback against the CPM alone (batched, and
     one lattice at a time), both at <= 5% error on the same statistics."""
@@ -761,8 +763,10 @@ def main():
                     choices=sorted(WORKLOADS) + sorted(ENSEMBLES) + sorted(EMULATOR))
     ap.add_argument("--emu-runs", type=int, default=100000, help="training runs of the emulator")
     ap.add_argument("--emu-eval", type=int, default=256, help="held-out points with replicate truth")
-    ap.add_argument("--emu-block", type=int, default=1 << 20, help="query points per sweep step (config 5: 1M)")
+    ap.add_argument("--emu-block", type=int, default=1 << 20, help="query points per sweep step (the full sweep: 1M)")
     ap.add_argument("--no-sweep", action="store_true", help="default workload: skip the embedded emulator sweep")
+    ap.add_argument("--clocks-csv", default=None, help="where to keep the raw nvidia-smi clock samples of the timed "
+                    "region (default: a temporary file)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -160,7 +160,7 @@ def place_cubes(lattice: np.ndarray, centres: np.ndarray, edge: int) -> int:
 # the workloads
 # --------------------------------------------------------------------------
 
-def config1_2d(seed: int = 1, n: int = 200, n_cells: int = 100, a: int = 4, c: int = 2,
+def point_cells_2d(seed: int = 1, n: int = 200, n_cells: int = 100, a: int = 4, c: int = 2,
                P: int = 1, n_mcs: int = 500) -> Workload:
     """2D CPM, n x n lattice, Moore-8, periodic; one-pixel cells at distinct
     uniform random sites; target volume 100; J(cell,cell)=20,
@@ -180,7 +180,7 @@ def config1_2d(seed: int = 1, n: int = 200, n_cells: int = 100, a: int = 4, c: i
                     at, la, ma, 20.0, 1, a, c, P, seed, 2, lat, ct, None, n_mcs)
 
 
-def config2_3d(seed: int = 1, n: int = 256, spacing: float = 10.0, a: int = 8, c: int = 2,
+def cube_cells_3d(seed: int = 1, n: int = 256, spacing: float = 10.0, a: int = 8, c: int = 2,
                P: int = 2, n_mcs: int = 1000) -> Workload:
     """3D CPM, n^3 lattice, 26-neighbourhood, periodic; 3^3 cubes at
     blue-noise centres (jittered grid, spacing 10, jitter 2: about 16,000
@@ -205,10 +205,10 @@ def config2_3d(seed: int = 1, n: int = 256, spacing: float = 10.0, a: int = 8, c
                     la, ma, 20.0 * S, S, a, c, P, seed, 2, lat, ct, None, n_mcs)
 
 
-# Target surface for config 3.  The paper gives none for this workload; it is
+# Target surface of the 3D fibre tissue.  The paper gives none for this workload; it is
 # fixed at 1.2x the 26-neighbourhood interface count of a digital ball of about
 # 800 voxels (radius 5.75: 799 voxels, 3,866 interfaces), i.e. 4,639.
-CONFIG3_A_TARGET = 4639
+TISSUE_A_TARGET = 4639
 
 
 def fibre_mask(shape, rng, cell_spacing: float = 48.0, frac: float = 0.15,
@@ -262,7 +262,7 @@ def fibre_mask(shape, rng, cell_spacing: float = 48.0, frac: float = 0.15,
     return (gap < thr.half()).cpu().numpy()
 
 
-def config3_3d(seed: int = 1, n: int = 1024, a: int = 8, c: int = 2, P: int = 2,
+def fibre_tissue_3d(seed: int = 1, n: int = 1024, a: int = 8, c: int = 2, P: int = 2,
                n_mcs: int = 200, device: Optional[str] = None,
                fibre_spacing: float = 48.0) -> Workload:
     """3D tissue-scale CPM with a frozen Voronoi-edge fibre network (about 15%
@@ -289,7 +289,7 @@ def config3_3d(seed: int = 1, n: int = 1024, a: int = 8, c: int = 2, P: int = 2,
     lv[1] = 25 * S
     vt[1] = 800
     lp[1] = 1            # 0.2 * S
-    at[1] = CONFIG3_A_TARGET
+    at[1] = TISSUE_A_TARGET
     la[1] = 200 * S
     ma[1] = 30
     ct = np.ones(nc + 1, dtype=np.uint8)
@@ -349,7 +349,7 @@ def random_small(seed: int, dim: int = 2, n: int = 16, n_cells: int = 6, edge: i
 
 
 # --------------------------------------------------------------------------
-# config 4: an ensemble for parameter sweeps
+# an ensemble for parameter sweeps
 # --------------------------------------------------------------------------
 
 SWEEP_RANGES = {            # the seven swept parameters, in model units
@@ -377,7 +377,7 @@ def latin_hypercube(n: int, rng) -> dict:
 
 def ensemble(n: int = 512, seed: int = 1, dim: Optional[int] = None, side2=(64, 512), side3=(64, 128),
              cells=(10, 2000), a: int = 4, c: int = 2) -> list:
-    """Config 4: n lattices of uneven sizes (log-uniform edge, 2D or 3D),
+    """Parameter-sweep ensemble: n lattices of uneven sizes (log-uniform edge, 2D or 3D),
     10..2000 cells each, parameters from a Latin hypercube (SWEEP_RANGES,
     scaled by SWEEP_SCALE).  Targets: V_t = half the lattice per cell (at
     least 10 sites); A_t = 1.2x an estimate of a compact cell's interface
@@ -423,7 +423,7 @@ def ensemble(n: int = 512, seed: int = 1, dim: Optional[int] = None, side2=(64, 
 
 
 # --------------------------------------------------------------------------
-# config 5: inputs of the emulator (swept parameters, network initialisation)
+# inputs of the emulator (swept parameters, network initialisation)
 # --------------------------------------------------------------------------
 
 EMULATOR_PARAMS = list(SWEEP_RANGES)      # input order of the emulator
@@ -454,9 +454,9 @@ def emulator_run(theta, seed: int, side: int = EMULATOR_SIDE, n_cells: int = EMU
                  c: int = 2) -> Workload:
     """One run of the emulator's training set: a 2D side x side periodic
     lattice, Moore neighbourhood, n_cells cells started as 3 x 3 squares at
-    jittered-grid centres (the config-4 recipe at fixed size and cell count),
+    jittered-grid centres (the ensemble recipe at fixed size and cell count),
     parameters theta (model units, EMULATOR_PARAMS order), S = SWEEP_SCALE,
-    the checkerboard of config 4 (a x a areas, c x c colours, one round per
+    the ensemble's checkerboard (a x a areas, c x c colours, one round per
     colour visit).  The seed fixes the start and the Philox key."""
     rng = np.random.default_rng(seed)
     th = dict(zip(EMULATOR_PARAMS, np.asarray(theta, dtype=np.float64)))

@@ -69,8 +69,10 @@ __device__ __forceinline__ int act_value(uint8_t stamp, uint32_t t8, int max_act
 
 // Integer geometric mean of Act (Q16) over site (x,y,z) with id sigma and its
 // same-cell Moore neighbours: EXPQ[(sum LN / count) >> 6]; 0 for the medium
-// or when any of those Act values is 0.
-template <int DIM>
+// or when any of those Act values is 0.  ROLL is the code-size level of the
+// calling kernel (see round_attempt): the stencil loops are rolled from the
+// outside in as it rises; the visiting order and the result do not change.
+template <int DIM, int ROLL>
 __device__ int64_t gm_q(const RoundArgs &a, const SmemTables &sm, uint32_t x, uint32_t y, uint32_t z, int32_t sigma,
                         int max_act)
 {
@@ -80,9 +82,9 @@ __device__ int64_t gm_q(const RoundArgs &a, const SmemTables &sm, uint32_t x, ui
     around(y, a.ny, ys);
     if (DIM == 3) around(z, a.nz, zs); else zs[0] = zs[1] = zs[2] = 0;
     int32_t sum = 0, cnt = 0;
-#pragma unroll
+#pragma unroll(ROLL >= 1 ? 1 : 3)
     for (int dz = (DIM == 3 ? 0 : 1); dz < (DIM == 3 ? 3 : 2); ++dz) {
-#pragma unroll
+#pragma unroll(ROLL >= 2 ? 1 : 3)
         for (int dy = 0; dy < 3; ++dy) {
             const uint32_t row = a.nx * (ys[dy] + a.ny * zs[dz]);
 #pragma unroll
@@ -114,8 +116,11 @@ __device__ __forceinline__ int64_t floor_div_pos(int64_t num, int64_t den)
 // in the same order, as the replay: chemotaxis
 // e = ((double)(-16 lambda (d . C_q)) / 16384) * (1/|d|), persistence
 // e = ((d_x p_x + d_y p_y + d_z p_z) * (double)(-16 lambda)) * (1/|d|).
+// Kept out of line: the round kernels call it only when a field or a
+// persistence direction is set, and inlining its FP64 code into every round
+// kernel enlarges them (instruction-fetch stalls).
 template <int DIM>
-__device__ __forceinline__ int64_t motility_q(const RoundArgs &a, int32_t si, int32_t sj, int ti, int tj, int ox,
+__device__ __noinline__ int64_t motility_q(const RoundArgs &a, int32_t si, int32_t sj, int ti, int tj, int ox,
                                               int oy, int oz, uint32_t isite)
 {
     const int32_t m = si > 0 ? si : sj;
@@ -144,7 +149,18 @@ __device__ __forceinline__ int64_t motility_q(const RoundArgs &a, int32_t si, in
 // One copy attempt of active block (ix, iy, iz) (active index i) in the round
 // described by a; also carries the previous round's change of index i into
 // the next tallies.  Returns whether the copy was accepted.
-template <int DIM, bool PERIM, bool ACT>
+//
+// ROLL is a code-size level.  The fully unrolled stencil loops make the Act
+// kernels large enough that instruction fetch stalls them (a warp's lanes sit
+// in different phases of the attempt), so those kernels roll loops from the
+// outside in: level 1 (single-lattice Act kernels, batched 2D Act kernel)
+// rolls the outer (z) loops of the neighbour sum and of the geometric mean;
+// level 2 (batched 3D Act kernel, whose CTAs mix lattices) also rolls the
+// middle (y) loops and runs the two geometric means through one copy of the
+// code.  Level 0 (kernels without Act) stays fully unrolled.  The level
+// changes only the code layout: every sum visits the same sites in the same
+// order.
+template <int DIM, bool PERIM, bool ACT, int ROLL>
 __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTables &sm, uint32_t ix, uint32_t iy,
                                               uint32_t iz, uint32_t i)
 {
@@ -187,9 +203,9 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
                 const int tj = type_of(sj, a.cell_type, a.tp.obstacle_type);
                 int32_t adhesion = 0;
                 int mi = 0, mj = 0;
-#pragma unroll
+#pragma unroll(ROLL >= 1 ? 1 : 3)
                 for (int dz = (DIM == 3 ? 0 : 1); dz < (DIM == 3 ? 3 : 2); ++dz) {
-#pragma unroll
+#pragma unroll(ROLL >= 2 ? 1 : 3)
                     for (int dy = 0; dy < 3; ++dy) {
                         const uint32_t row = a.nx * (ys[dy] + a.ny * zs[dz]);
 #pragma unroll
@@ -236,8 +252,22 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
                         else if (lo >= a.L || (lo > 0 && w.v[2] >= __ldg(a.thr + lo))) decided = 0;
                         else {
                             const uint32_t ix_ = xs[ox], iy_ = ys[oy], iz_ = zs[oz];
-                            const int64_t gi = gm_q<DIM>(a, sm, ix_, iy_, iz_, si, si > 0 ? sm.ma[ti] : 0);
-                            const int64_t gj = gm_q<DIM>(a, sm, jx, jy, jz, sj, sj > 0 ? sm.ma[tj] : 0);
+                            int64_t gi = 0, gj = 0;
+                            if (ROLL >= 2) {
+                                // source then target through one copy of the code
+#pragma unroll 1
+                                for (int q = 0; q < 2; ++q) {
+                                    const bool src = q == 0;
+                                    const int64_t g =
+                                        gm_q<DIM, ROLL>(a, sm, src ? ix_ : jx, src ? iy_ : jy, src ? iz_ : jz,
+                                                        src ? si : sj,
+                                                        src ? (si > 0 ? sm.ma[ti] : 0) : (sj > 0 ? sm.ma[tj] : 0));
+                                    if (src) gi = g; else gj = g;
+                                }
+                            } else {
+                                gi = gm_q<DIM, ROLL>(a, sm, ix_, iy_, iz_, si, si > 0 ? sm.ma[ti] : 0);
+                                gj = gm_q<DIM, ROLL>(a, sm, jx, jy, jz, sj, sj > 0 ? sm.ma[tj] : 0);
+                            }
                             dhq += floor_div_pos(lam * (gj - gi), mx * 4096);
                         }
                     }
@@ -259,9 +289,10 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
 
 // Resident CTAs per SM (register budget): the round kernel is latency-bound.
 // Measured on GB300 in same-box A/B runs: without Act, four CTAs of 256
-// (64 registers) are fastest (config 2: 1.05 ms per MCS against 1.31 at 32
-// registers); with Act, eight (32 registers, a few spills) are fastest
-// (1024^3 tissue: 147 ms per MCS against 173 at 64 registers).
+// (64 registers) are fastest (256^3 cube cells: 1.05 ms per MCS against 1.31
+// at 32 registers); with Act, eight (32 registers, a few spills) are fastest
+// (1024^3 fibre tissue: slower at 40, 48 and 64 registers, whose lower
+// occupancy costs more than the spills they save).
 #ifndef CPM_ROUND_MIN_BLOCKS
 #define CPM_ROUND_MIN_BLOCKS 4
 #endif
@@ -291,7 +322,7 @@ __global__ void __launch_bounds__(kThreads, ACT ? CPM_ROUND_MIN_BLOCKS_ACT : CPM
     const uint32_t i = ix + a.nax * (iy + a.nay * iz);
     bool accepted = false;
     if (valid) {
-        accepted = round_attempt<DIM, PERIM, ACT>(a, sm, ix, iy, iz, i);
+        accepted = round_attempt<DIM, PERIM, ACT, ACT ? 1 : 0>(a, sm, ix, iy, iz, i);
     }
     const unsigned m = __ballot_sync(0xffffffffu, accepted);
     if ((threadIdx.x & 31) == 0 && m != 0) atomicAdd(a.accepts, (unsigned long long)__popc(m));
@@ -362,7 +393,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, ACT ? CPM_BATCH_MIN_BLOCKS_A
     bool accepted = false;
     if (threadIdx.x < bx_ * by_ * bz_ && ix < ra.nax && iy < ra.nay && iz < naz) {
         const uint32_t i = ix + ra.nax * (iy + ra.nay * iz);
-        accepted = round_attempt<DIM, PERIM, ACT>(ra, sm, ix, iy, iz, i);
+        accepted = round_attempt<DIM, PERIM, ACT, ACT ? (DIM == 3 ? 2 : 1) : 0>(ra, sm, ix, iy, iz, i);
     }
     const unsigned m = __ballot_sync(0xffffffffu, accepted);
     if ((threadIdx.x & 31) == 0 && m != 0) atomicAdd(ra.accepts, (unsigned long long)__popc(m));

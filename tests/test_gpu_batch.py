@@ -76,7 +76,7 @@ def test_batch_3d_mixed_bit_exact(cpm):
 
 
 def test_batch_of_the_ensemble_workload(cpm):
-    """Ten members of the parameter-sweep ensemble (config 4 recipe, small
+    """Ten members of the parameter-sweep ensemble (its recipe with small
     edges), bit-exact after 3 MCS; the Act stamps cross a clamp at MCS 0."""
     ws = cw.ensemble(10, seed=5, dim=2, side2=(32, 96), cells=(4, 40))
     batch = cpm.Batch(ws)

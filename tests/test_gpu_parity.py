@@ -83,7 +83,7 @@ def test_bit_exact_against_replay(cpm, name, factory, n_mcs):
 
 def test_non_cubic_lattice(cpm):
     """Extents that differ per axis (ragged number of active blocks per CTA)."""
-    w = cw.config2_3d(seed=3, n=24, a=4, c=2, P=8)
+    w = cw.cube_cells_3d(seed=3, n=24, a=4, c=2, P=8)
     lat = np.zeros((8, 12, 20), dtype=np.int32)
     lat[:] = w.lattice[:8, :12, :20]
     ids = np.unique(lat[lat > 0])
@@ -159,7 +159,7 @@ def test_empty_and_degenerate_lattices(cpm):
     assert sim.stats()["accepts"] == 0
     assert np.array_equal(sim.read_lattice(), lat)
     # single-pixel cells must never vanish
-    w2 = cw.config1_2d(seed=3, n=40, n_cells=30, a=4, c=2, P=1)
+    w2 = cw.point_cells_2d(seed=3, n=40, n_cells=30, a=4, c=2, P=1)
     w2.v_target[1] = 1
     w2.lambda_v[1] = 1
     sim = cpm.Sim(w2)
@@ -171,16 +171,16 @@ def test_empty_and_degenerate_lattices(cpm):
     assert np.all(V[1:] >= 1)
 
 
-def test_config1_full_size_bit_exact(cpm):
+def test_point_cells_200_full_size_bit_exact(cpm):
     """The 200x200 2D workload as specified (Moore-8, 100 cells, V_t = 100),
     bit-exact over 20 MCS."""
-    w = cw.config1_2d(seed=1)
+    w = cw.point_cells_2d(seed=1)
     sim = cpm.Sim(w)
     ref = oracle.State(w)
     for m in range(20):
         sim.step(1)
         ref.replay_run(1)
-    _compare(sim, ref, "config1 after 20 MCS")
+    _compare(sim, ref, "200^2 point cells after 20 MCS")
 
 
 def test_load_lattice_resets_tallies(cpm):
@@ -197,10 +197,10 @@ def test_load_lattice_resets_tallies(cpm):
     assert torch.equal(out, d)
 
 
-def test_config3_tissue_small_bit_exact(cpm):
+def test_tissue_64_bit_exact(cpm):
     """The tissue workload (fibre obstacles, Act, perimeter, 26-neighbourhood)
     at 64^3, bit-exact after every MCS."""
-    w = cw.config3_3d(seed=2, n=64, a=4, c=2, P=8, device="cuda")
+    w = cw.fibre_tissue_3d(seed=2, n=64, a=4, c=2, P=8, device="cuda")
     assert (w.lattice < 0).mean() > 0.1
     sim = cpm.Sim(w)
     ref = oracle.State(w)
@@ -211,14 +211,14 @@ def test_config3_tissue_small_bit_exact(cpm):
     assert sim.verify() == 0
 
 
-def test_config3_full_size_sampled(cpm):
+def test_tissue_1024_sampled(cpm):
     """1024^3 tissue workload in the launch configuration bench.py times
     (a=4, c=2, P=8: one round per sub-pass).  After 2 MCS and 3 sub-passes,
     one more round runs on the GPU; the oracle replays that round for 4,096
     sampled active blocks from the GPU's state before it, and their sites and
     Act values must match.  Tallies are checked at full size by a device
     recount, obstacles by comparison with the input."""
-    w = cw.config3_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda")
+    w = cw.fibre_tissue_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda")
     sim = cpm.Sim(w)
     sim.step(2)
     sim.step_subpasses(3)
@@ -272,9 +272,9 @@ TILE_CASES = [
      .replace(tile=8, tile_cycles=1), 2),
     ("3d_T8_PT2_act_obst", lambda: cw.random_small(35, dim=3, n=16, n_cells=12, perimeter=True, act=True,
                                                    obstacles=0.05, a=4, c=2, P=8).replace(tile=8, tile_cycles=2), 2),
-    ("3d_tissue_T16", lambda: cw.config3_3d(seed=3, n=64, a=4, c=2, P=8, device="cuda")
+    ("3d_tissue_T16", lambda: cw.fibre_tissue_3d(seed=3, n=64, a=4, c=2, P=8, device="cuda")
      .replace(tile=16, tile_cycles=1), 2),
-    ("3d_cfg2_T24", lambda: cw.config2_3d(seed=4, n=96, a=4, c=2, P=8).replace(tile=24, tile_cycles=2), 2),
+    ("3d_cubes_T24", lambda: cw.cube_cells_3d(seed=4, n=96, a=4, c=2, P=8).replace(tile=24, tile_cycles=2), 2),
 ]
 
 

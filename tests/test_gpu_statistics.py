@@ -72,7 +72,7 @@ def summarise(snapshots, tallies, accepts, n_sites, n_cells, shape):
 def run_serial(args):
     seed, a = args
     import oracle
-    w = cw.config1_2d(seed=seed, a=a, c=2, P=1)  # the schedule does not enter the serial chain
+    w = cw.point_cells_2d(seed=seed, a=a, c=2, P=1)  # the schedule does not enter the serial chain
     st = oracle.State(w)
     st.serial_run(BURN)
     snaps, tall, acc = [st.lattice.copy()], [], 0
@@ -84,7 +84,7 @@ def run_serial(args):
 
 
 def run_gpu(cpm, seed, a, P):
-    w = cw.config1_2d(seed=seed, a=a, c=2, P=P)
+    w = cw.point_cells_2d(seed=seed, a=a, c=2, P=P)
     sim = cpm.Sim(w)
     sim.step(BURN)
     snaps, tall = [sim.read_lattice()], []

@@ -34,8 +34,8 @@ def cpm():
 
 
 CASES = [
-    ("3d_perim", lambda: cw.config2_3d(seed=5, n=32, a=4, c=2, P=8), 3),
-    ("2d_config1", lambda: cw.config1_2d(seed=2, n=200, a=4, c=2, P=1), 8),
+    ("3d_perim", lambda: cw.cube_cells_3d(seed=5, n=32, a=4, c=2, P=8), 3),
+    ("2d_points_200", lambda: cw.point_cells_2d(seed=2, n=200, a=4, c=2, P=1), 8),
     ("3d_obstacles_a8", lambda: cw.random_small(21, dim=3, n=16, n_cells=10, edge=4, perimeter=True,
                                                 obstacles=0.05, a=8, c=2, P=2, T=30.0), 5),
 ]
@@ -81,7 +81,7 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(cpm):
     lib = cpm.load()
     dummy = torch.zeros(16, dtype=torch.int32, device="cuda")
     # 256^3 with a = 2... : 128^3 / 8 > 262,144 active blocks per round
-    w = cw.config1_2d(seed=1, n=8, n_cells=2, a=4)
+    w = cw.point_cells_2d(seed=1, n=8, n_cells=2, a=4)
     keep = []
     cfg = cpm.make_config(w, keep)
     cfg.dim, cfg.nx, cfg.ny, cfg.nz = 3, 1024, 1024, 512
