@@ -116,6 +116,46 @@ def test_gemm_against_fp64(lib, ta, tb, case, epi, c_f32):
     assert np.all(err <= bound), (float(err.max()), float((err / bound).max()))
 
 
+@pytest.mark.parametrize("tb", [1, 0])
+@pytest.mark.parametrize("epi", [1, 2])
+def test_gelu_epilogue_within_the_erf_bound(lib, tb, epi):
+    """The GELU (epi 1) and GELU' (epi 2) epilogues on a dense grid of bf16
+    inputs in [-10, 10], against float64.  acc is made exact (one nonzero
+    column of ones), so the error is the epilogue's own: erf from Abramowitz &
+    Stegun 7.1.26 (|e| <= 1.5e-7) with float32 rounding and the fast
+    reciprocal and exponential, bounded by 4e-7 max(1, |z|).  tb = 1 takes the
+    tcgen05 forward path for epi 1, tb = 0 the mma.sync kernel."""
+    grid = np.unique(torch.tensor(np.linspace(-10, 10, 6001), dtype=torch.float32)
+                     .to(torch.bfloat16).double().numpy())
+    M, N, K = len(grid), 16, 16
+    a = np.zeros((M, K))
+    a[:, 0] = grid if epi == 1 else 1.0
+    A, _ = _bf16(a)
+    b = np.zeros((N, K) if tb else (K, N))
+    if tb:
+        b[:, 0] = 1.0
+    else:
+        b[0, :] = 1.0
+    B, _ = _bf16(b)
+    bias = torch.zeros((1, N), dtype=torch.float32).cuda()
+    Zin = torch.tensor(np.repeat(grid[:, None], N, axis=1), dtype=torch.float32).cuda().contiguous()
+    Zout = torch.full((M, N), np.nan, dtype=torch.float32).cuda()
+    C = torch.zeros((M, N), dtype=torch.float32).cuda()
+    Z = Zout if epi == 1 else Zin
+    rc = lib.cpm_mlp_gemm(0, tb, M, N, K, 1, _p(A), K, 0, _p(B), K if tb else N, 0,
+                          _p(bias) if epi == 1 else None, 0, _p(C), 1, N, 0, _p(Z), N, 0, epi, None)
+    assert rc == 0
+    torch.cuda.synchronize()
+    z = grid[:, None]
+    exp = omlp.gelu(z) if epi == 1 else omlp.gelu_grad(z)
+    got = C.double().cpu().numpy()
+    err = np.abs(got - exp)
+    bound = 4e-7 * np.maximum(1.0, np.abs(z))
+    assert np.all(err <= bound), (float(err.max()), float(grid[np.argmax(err.max(axis=1))]))
+    if epi == 1:
+        np.testing.assert_array_equal(Zout.double().cpu().numpy(), np.repeat(z, N, axis=1))
+
+
 SIZES = [7, 256, 256, 256, 256, 16]
 
 
