@@ -194,8 +194,9 @@ int cpm_verify(cpm_handle *h, int64_t *n_mismatch);
 /* Number of kernel launches the library has issued for this handle. */
 int64_t cpm_kernel_launches(const cpm_handle *h);
 
-/* Message of the last failed call on h (or of the last failed cpm_create
- * when h is NULL).  The string stays valid until the next call on h. */
+/* Message of the last failed call on h (or, when h is NULL, of the calling
+ * thread's last failed cpm_create).  The string stays valid until the next
+ * call on h (with NULL: the thread's next cpm_create). */
 const char *cpm_last_error(const cpm_handle *h);
 
 /* Free every resource of h (NULL is ignored).  Synchronises the stream. */
@@ -292,8 +293,8 @@ int cpm_batch_summarize(cpm_batch *b, const int64_t *cells_hist, const int64_t *
 /* Kernel launches issued for b (set-up included). */
 int64_t cpm_batch_kernel_launches(const cpm_batch *b);
 
-/* Message of the last failed call on b (of the last failed cpm_batch_create
- * when b is NULL). */
+/* Message of the last failed call on b (of the calling thread's last failed
+ * cpm_batch_create when b is NULL). */
 const char *cpm_batch_last_error(const cpm_batch *b);
 
 /* Free b and all its lattices (NULL is ignored).  Synchronises the stream. */

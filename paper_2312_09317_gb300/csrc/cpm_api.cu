@@ -64,7 +64,7 @@ struct cpm_handle {
 
 namespace {
 
-std::string g_create_error;
+thread_local std::string g_create_error;  // per calling thread: creations may run concurrently
 
 int fail(cpm_handle *h, int code, const char *fmt, ...)
 {
@@ -866,7 +866,7 @@ struct cpm_batch {
 };
 
 namespace {
-std::string g_batch_create_error;
+thread_local std::string g_batch_create_error;  // per calling thread, as g_create_error
 
 int bfail(cpm_batch *b, int code, const std::string &msg)
 {

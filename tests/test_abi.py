@@ -122,3 +122,30 @@ def test_motility_settings_are_checked_without_a_gpu(lib):
     wp = cw.with_motility(w, lambda_pers=5, mu=1.5, dt=2)
     rc, err = _create(wp)
     assert rc == cpm.CPM_E_INVALID and "mu_pers" in err
+
+
+def test_create_errors_are_per_thread(lib):
+    """cpm_last_error(NULL) reports the calling thread's own failed create,
+    even when another thread fails in between."""
+    import threading
+    w = cw.random_small(1, dim=2, n=16, n_cells=3, a=4, c=2, P=1)
+    gate = threading.Barrier(2)
+    seen = {}
+
+    def worker(name, field, value):
+        keep = []
+        c = cpm.make_config(w, keep)
+        setattr(c, field, value)
+        h = ctypes.c_void_p()
+        rc = lib.cpm_create(ctypes.byref(c), None, ctypes.byref(h))
+        gate.wait()  # both creates have failed before either message is read
+        seen[name] = (rc, lib.cpm_last_error(None).decode())
+
+    ts = [threading.Thread(target=worker, args=("dim", "dim", 4)),
+          threading.Thread(target=worker, args=("temp", "temperature", 0.0))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert seen["dim"][0] == cpm.CPM_E_INVALID and "dim" in seen["dim"][1]
+    assert seen["temp"][0] == cpm.CPM_E_INVALID and "temperature" in seen["temp"][1]
