@@ -123,6 +123,8 @@ int cpm_mlp_predict(cpm_mlp *h, const float *X, int64_t n_rows, float *mean_out,
 
 /* Kernels launched by this handle so far. */
 uint64_t cpm_mlp_kernel_launches(const cpm_mlp *h);
+/* Message of the last failed call on h; with h NULL, of the calling thread's
+ * last failed cpm_mlp_create. */
 const char *cpm_mlp_last_error(const cpm_mlp *h);
 int cpm_mlp_destroy(cpm_mlp *h);
 

@@ -744,6 +744,15 @@ int fail(cpm_mlp *h, int code, const char *msg)
     return code;
 }
 
+// Message of the calling thread's last failed cpm_mlp_create (no handle exists then).
+thread_local char g_create_err[256] = "";
+
+int create_fail(int code, const char *msg)
+{
+    snprintf(g_create_err, sizeof g_create_err, "%s", msg);
+    return code;
+}
+
 int cuda_check(cpm_mlp *h, cudaError_t e, const char *what)
 {
     if (e == cudaSuccess) return CPM_MLP_OK;
@@ -913,14 +922,15 @@ int64_t cpm_mlp_param_count(const cpm_mlp_shape *s)
 
 int cpm_mlp_create(const cpm_mlp_shape *shape, const float *init_params, void *cuda_stream, cpm_mlp **out)
 {
-    if (!shape || !init_params || !out) return CPM_MLP_E_INVALID;
+    if (!shape || !init_params || !out) return create_fail(CPM_MLP_E_INVALID, "shape, init_params and out are required");
     *out = nullptr;
     const int64_t P = cpm_mlp_param_count(shape);
     if (P < 0 || shape->n_members < 1 || shape->n_members > 64 || shape->max_rows < 1 || shape->width % 8 ||
         shape->max_rows > (1 << 22))
-        return CPM_MLP_E_INVALID;
+        return create_fail(CPM_MLP_E_INVALID,
+                           "invalid shape (members 1..64, width a multiple of 8, hidden layers 1..15, rows 1..2^22)");
     cpm_mlp *h = new (std::nothrow) cpm_mlp();
-    if (!h) return CPM_MLP_E_NOMEM;
+    if (!h) return create_fail(CPM_MLP_E_NOMEM, "host allocation failed");
     h->sh = *shape;
     h->st = (cudaStream_t)cuda_stream;
     h->n_layers = shape->n_hidden + 1;
@@ -950,10 +960,11 @@ int cpm_mlp_create(const cpm_mlp_shape *shape, const float *init_params, void *c
     if (rc) {
         release(h);
         delete h;
-        return CPM_MLP_E_NOMEM;
+        return create_fail(CPM_MLP_E_NOMEM, "device allocation failed");
     }
     if (cpm_mlp_set_params(h, init_params) != CPM_MLP_OK ||
         cudaMemsetAsync(h->bad, 0, 2 * sizeof(int), h->st) != cudaSuccess) {
+        create_fail(CPM_MLP_E_CUDA, h->err[0] ? h->err : "initial upload failed");
         release(h);
         delete h;
         return CPM_MLP_E_CUDA;
@@ -1094,7 +1105,7 @@ int cpm_mlp_predict(cpm_mlp *h, const float *X, int64_t n_rows, float *mean_out,
 
 uint64_t cpm_mlp_kernel_launches(const cpm_mlp *h) { return h ? h->launches : 0; }
 
-const char *cpm_mlp_last_error(const cpm_mlp *h) { return h ? h->err : "null handle"; }
+const char *cpm_mlp_last_error(const cpm_mlp *h) { return h ? h->err : g_create_err; }
 
 int cpm_mlp_destroy(cpm_mlp *h)
 {

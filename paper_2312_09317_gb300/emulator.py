@@ -85,7 +85,7 @@ class Ensemble:
         rc = lib.cpm_mlp_create(ctypes.byref(self.shape), init.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(st),
                                 ctypes.byref(h))
         if rc != 0:
-            raise cpm.CPMError(rc, "cpm_mlp_create failed")
+            raise cpm.CPMError(rc, "cpm_mlp_create: " + lib.cpm_mlp_last_error(None).decode())
         self.h = h
         self.sizes = [n_in] + [width] * n_hidden + [n_out]
 

@@ -99,3 +99,25 @@ def test_mlp_init_layout():
 def test_statistic_order_matches_the_library():
     assert em.STATS == oobs.SUMMARY_STATS
     assert set(em.LOG_STATS) <= set(em.STATS)
+
+
+def test_invalid_network_shapes_are_rejected_without_a_gpu():
+    """cpm_mlp_create validates the shape before touching the device and
+    reports why through cpm_mlp_last_error(NULL)."""
+    import ctypes
+    from paper_2312_09317_gb300 import build as B
+    from paper_2312_09317_gb300 import cpm
+    B.build()
+    lib = cpm.load()
+    init = np.zeros(1 << 16, dtype=np.float32)
+    for shape in [cpm.MlpShape(0, 7, 256, 4, 16, 1024),     # no members
+                  cpm.MlpShape(5, 7, 250, 4, 16, 1024),     # width not a multiple of 8
+                  cpm.MlpShape(5, 7, 256, 16, 16, 1024),    # too many layers
+                  cpm.MlpShape(5, 7, 256, 4, 16, 1 << 23)]:  # too many rows
+        h = ctypes.c_void_p()
+        rc = lib.cpm_mlp_create(ctypes.byref(shape), init.ctypes.data_as(ctypes.c_void_p), None, ctypes.byref(h))
+        assert rc == -1 and not h.value
+        assert b"invalid shape" in lib.cpm_mlp_last_error(None)
+    h = ctypes.c_void_p()
+    assert lib.cpm_mlp_create(None, None, None, ctypes.byref(h)) == -1
+    assert b"required" in lib.cpm_mlp_last_error(None)
