@@ -314,9 +314,14 @@ void cpm_batch_destroy(cpm_batch *b);
  *              tallies of that lattice on entry (e.g. from cpm_read_tallies),
  *              updated in place;
  *   cell_type  device, n_cells + 1 uint8.
- * cfg gives the model and schedule (its host pointer fields are ignored; the
- * lattice contents are not validated; only the global schedule, tile = 0).  The result equals what a handle at
- * the same position would produce with cpm_step_subpasses.
+ * cfg gives the model and schedule (its host pointer fields are ignored;
+ * only the global schedule, tile = 0; at most 2^31 sites).  The result
+ * equals what a handle at the same position would produce with
+ * cpm_step_subpasses.
+ * Precondition, not checked (cpm_create checks it for handles): every
+ * lattice value lies in -1..n_cells and every cell_type entry is below
+ * CPM_MAX_TYPES.  A violation is undefined behaviour: the kernel would index
+ * the tallies and the type tables out of bounds.
  *
  * It allocates nothing: all scratch (second tally buffer, pending-change
  * buffers, threshold/log/exp tables, accept counter) lives in one fixed
@@ -328,7 +333,10 @@ void cpm_batch_destroy(cpm_batch *b);
  * Act term.
  * The first call on a device looks up the array's device address with that
  * device current (a one-time set-up); make that first call before any stream
- * capture.  Every call shares the array and finds the previous call's
+ * capture.  A call on a stream that is capturing returns CPM_E_INVALID: its
+ * table uploads read host memory that the next call rewrites.  The tables
+ * are built in static host buffers (not on the caller's stack) under a lock.
+ * Every call shares the array and finds the previous call's
  * contents there; the call re-initialises everything it reads, but calls
  * that overlap on the GPU (other streams, other threads) race on it and must
  * be serialised by the caller.  Work is queued on cuda_stream; when accepts

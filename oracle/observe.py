@@ -158,15 +158,20 @@ def summary_statistics(cells, member, n_cells, shape, v_target, a_target, every,
     anchor, V, A = cells[..., 0], cells[..., 1], cells[..., 5]
     alive = V > 0
     out = np.full((n, len(SUMMARY_STATS)), np.nan)
-    out[:, 0] = _masked_mean(V, alive, (0, 2)) / v_target
-    out[:, 2] = _masked_mean(A, alive, (0, 2)) / a_target
+    # statistics scaled by a target of 0 (no such constraint) stay NaN (undefined)
+    if v_target != 0:
+        out[:, 0] = _masked_mean(V, alive, (0, 2)) / v_target
+    if a_target != 0:
+        out[:, 2] = _masked_mean(A, alive, (0, 2)) / a_target
     with np.errstate(invalid="ignore", divide="ignore"):
         vm = _masked_mean(V, alive, 2)
         am = _masked_mean(A, alive, 2)
         vv = _masked_mean((V - vm[..., None]) ** 2, alive, 2)
         av = _masked_mean((A - am[..., None]) ** 2, alive, 2)
-    out[:, 1] = np.sqrt(np.nanmean(vv, axis=0)) / v_target
-    out[:, 3] = np.sqrt(np.nanmean(av, axis=0)) / a_target
+    if v_target != 0:
+        out[:, 1] = np.sqrt(np.nanmean(vv, axis=0)) / v_target
+    if a_target != 0:
+        out[:, 3] = np.sqrt(np.nanmean(av, axis=0)) / a_target
     # centroids: anchor + offset mean, unwrapped across snapshots
     Vs = np.where(alive, V, 1.0)
     ax = np.mod(anchor, nx)

@@ -45,6 +45,16 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 unsigned char *g_scratch_addr[kMaxDevices] = {nullptr};
+
+// Host copies of the integer tables, built by each call under g_table_mutex
+// and uploaded from here (kept off the caller's stack: about 150 KiB, more
+// than some worker threads have).  A host-to-device cudaMemcpyAsync from
+// pageable memory returns once the source has been staged, so the next call
+// may rebuild them as soon as this call has issued its copies.
+std::mutex g_table_mutex;
+uint32_t g_thr[kNaMaxThr];
+int32_t g_ln[kLnEntries];
+int32_t g_expq[kNaMaxExpq];
 // Failures are reported by return code only (the message strings below are
 // for the reader): CPM_E_LIMIT when a size exceeds the static scratch,
 // CPM_E_INVALID for other bad arguments, CPM_E_CUDA for runtime errors.
@@ -92,6 +102,9 @@ extern "C" int cpm_step_noalloc(const cpm_config *cfg, int32_t *lattice, int32_t
     if ((uint32_t)c.a - s < 2) return na_fail(CPM_E_INVALID, "blocks of one colour must be >= 2 sites apart");
     if (c.nx % c.a || c.ny % c.a || (c.dim == 3 && c.nz % c.a))
         return na_fail(CPM_E_INVALID, "extents must be multiples of a");
+    // the round kernel indexes sites with 32-bit integers
+    if ((uint64_t)c.nx * (uint64_t)c.ny * (uint64_t)c.nz > (1ull << 31))
+        return na_fail(CPM_E_INVALID, "more than 2^31 sites");
     const uint32_t C = na_ipow((uint32_t)c.c, c.dim);
     if (C > 27) return na_fail(CPM_E_INVALID, "at most 27 colours");
     const uint32_t sd = na_ipow(s, c.dim);
@@ -115,27 +128,21 @@ extern "C" int cpm_step_noalloc(const cpm_config *cfg, int32_t *lattice, int32_t
     for (int a = 0; a < CPM_MAX_TYPES; a++) motility |= c.lambda_chem[a] != 0 || c.lambda_pers[a] != 0;
     if (motility) return na_fail(CPM_E_INVALID, "no motility terms here");
 
-    // integer tables, on the stack
-    uint32_t thr[kNaMaxThr];
+    // the threshold table must fit the scratch: L is the first h with THR[h] = 0
     int32_t L = 0;
-    for (;; L++) {
-        const double v = std::floor(std::ldexp(std::exp(-(double)L / (16.0 * c.temperature)), 32));
-        if (v <= 0.0) break;
-        if (L >= kNaMaxThr) return na_fail(CPM_E_LIMIT, "temperature too high for the scratch table");
-        thr[L] = v >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)v;
-    }
-    int32_t ln[kLnEntries];
-    ln[0] = 0;
-    for (int a = 1; a < kLnEntries; a++) ln[a] = (int32_t)std::llround(std::ldexp(std::log((double)a), 16));
-    const int32_t ne = (ln[kLnEntries - 1] >> 6) + 1;
-    if (ne > kNaMaxExpq) return na_fail(CPM_E_INVALID, "exp table too long");
-    int32_t expq[kNaMaxExpq];
-    for (int m = 0; m < ne; m++) expq[m] = (int32_t)std::llround(std::ldexp(std::exp((double)m / 1024.0), 16));
+    while (std::floor(std::ldexp(std::exp(-(double)L / (16.0 * c.temperature)), 32)) > 0.0)
+        if (++L > kNaMaxThr) return na_fail(CPM_E_LIMIT, "temperature too high for the scratch table");
+
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // the table uploads below read host memory that this call rebuilds next
+    // time, so a copy recorded into a graph would not keep its contents
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return na_fail(CPM_E_CUDA, "cudaStreamIsCapturing failed");
+    if (cap != cudaStreamCaptureStatusNone) return na_fail(CPM_E_INVALID, "the stream is capturing");
 
     unsigned char *scr = nullptr;
     int rc = scratch_for_current_device(&scr);
     if (rc) return rc;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     int4 *pend = (int4 *)(scr + kOffPend);
     int32_t *V1 = (int32_t *)(scr + kOffTally);
     int32_t *A1 = V1 + (kNaMaxCells + 1);
@@ -150,9 +157,22 @@ extern "C" int cpm_step_noalloc(const cpm_config *cfg, int32_t *lattice, int32_t
         if ((expr) != cudaSuccess) return na_fail(CPM_E_CUDA, #expr " failed"); \
     } while (0)
     // the scratch keeps the previous call's contents: set everything this call reads
-    NA_TRY(cudaMemcpyAsync(d_thr, thr, sizeof(uint32_t) * (size_t)L, cudaMemcpyHostToDevice, st));
-    NA_TRY(cudaMemcpyAsync(d_ln, ln, sizeof ln, cudaMemcpyHostToDevice, st));
-    NA_TRY(cudaMemcpyAsync(d_expq, expq, sizeof(int32_t) * (size_t)ne, cudaMemcpyHostToDevice, st));
+    {
+        std::lock_guard<std::mutex> lock(g_table_mutex);
+        for (int32_t h = 0; h < L; h++) {
+            const double v = std::floor(std::ldexp(std::exp(-(double)h / (16.0 * c.temperature)), 32));
+            g_thr[h] = v >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)v;
+        }
+        g_ln[0] = 0;
+        for (int a = 1; a < kLnEntries; a++) g_ln[a] = (int32_t)std::llround(std::ldexp(std::log((double)a), 16));
+        const int32_t ne = (g_ln[kLnEntries - 1] >> 6) + 1;
+        if (ne > kNaMaxExpq) return na_fail(CPM_E_INVALID, "exp table too long");
+        for (int m = 0; m < ne; m++)
+            g_expq[m] = (int32_t)std::llround(std::ldexp(std::exp((double)m / 1024.0), 16));
+        NA_TRY(cudaMemcpyAsync(d_thr, g_thr, sizeof(uint32_t) * (size_t)L, cudaMemcpyHostToDevice, st));
+        NA_TRY(cudaMemcpyAsync(d_ln, g_ln, sizeof g_ln, cudaMemcpyHostToDevice, st));
+        NA_TRY(cudaMemcpyAsync(d_expq, g_expq, sizeof(int32_t) * (size_t)ne, cudaMemcpyHostToDevice, st));
+    }
     NA_TRY(cudaMemsetAsync(pend, 0, sizeof(int4) * 2 * (size_t)n_active, st));
     NA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st));
     NA_TRY(cudaMemcpyAsync(V1, V, tb, cudaMemcpyDeviceToDevice, st));

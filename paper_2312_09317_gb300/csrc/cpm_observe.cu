@@ -291,13 +291,14 @@ __global__ void __launch_bounds__(kSumThreads) summarize_kernel(const ObserveIte
             nv += 1.0;
         }
     }
+    // a statistic scaled by a target of 0 (no volume or perimeter constraint) is undefined: NaN
     if (tn > 0.0) {
-        o[0] = tv / tn / it.v_ref;
-        o[2] = ta / tn / it.a_ref;
+        if (it.v_ref != 0.0) o[0] = tv / tn / it.v_ref;
+        if (it.a_ref != 0.0) o[2] = ta / tn / it.a_ref;
     }
     if (nv > 0.0) {
-        o[1] = sqrt(vv / nv) / it.v_ref;
-        o[3] = sqrt(av / nv) / it.a_ref;
+        if (it.v_ref != 0.0) o[1] = sqrt(vv / nv) / it.v_ref;
+        if (it.a_ref != 0.0) o[3] = sqrt(av / nv) / it.a_ref;
     }
     for (int j = 0; j < 3; ++j)
         if (acc[A_MSD + 3 + j] > 0.0) o[4 + j] = acc[A_MSD + j] / acc[A_MSD + 3 + j];

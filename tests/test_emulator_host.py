@@ -74,6 +74,26 @@ def test_statistics_of_resting_cells_and_a_vanished_cell():
     np.testing.assert_allclose(st["elongation"], 1.0)
 
 
+def test_statistics_scaled_by_a_zero_target_are_nan():
+    """Without a perimeter constraint (A_t = 0) the interface statistics
+    scaled by A_t are undefined: NaN, with no division warning; the volume
+    statistics are unaffected."""
+    import warnings
+    S1, n, C, nx = 11, 1, 2, 32
+    cells, member = _rows(S1, n, C)
+    for s in range(S1):
+        for c in range(C):
+            cells[s, 0, c + 1, :2] = [100 + 40 * c, 8]
+            cells[s, 0, c + 1, 5] = 12
+            cells[s, 0, c + 1, 6:8] = [8, 8]
+    with warnings.catch_warnings():
+        warnings.simplefilter("error")
+        out = oobs.summary_statistics(cells, member, C, (nx, nx), 8.0, 0.0, 10, nx * nx)
+    st = dict(zip(oobs.SUMMARY_STATS, out[0]))
+    assert np.isnan(st["perim_mean"]) and np.isnan(st["perim_sd"])
+    np.testing.assert_allclose(st["vol_mean"], 1.0)
+
+
 def test_sweep_points_are_on_the_simulated_grid_and_span_the_ranges():
     X = cw.sweep_points(200, 3)
     assert X.shape == (200, 7)

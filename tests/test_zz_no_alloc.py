@@ -77,6 +77,64 @@ def test_noalloc_matches_handle_path_twice(cpm, name, factory, n_sub):
     ref.close()
 
 
+def test_noalloc_matches_the_replay_oracle_from_mid_mcs(cpm):
+    """Against the CPU replay of the parallel scheme directly: a 2D lattice
+    with 6x6 areas (3x3 blocks, 9 rounds per colour visit: an odd count, so
+    the current tallies end in the scratch's second buffer), started at
+    sub-pass 3 of MCS 0 and advanced by two calls of 5 sub-passes each."""
+    import oracle
+    w = cw.random_small(31, dim=2, n=48, n_cells=14, edge=4, perimeter=True, obstacles=0.03, a=6, c=2, P=1,
+                        T=25.0)
+    st = oracle.State(w)
+    st.replay_subpasses(3)
+    lib = cpm.load()
+    keep = []
+    cfg = cpm.make_config(w, keep)
+    dev = torch.device("cuda")
+    lat = torch.from_numpy(st.lattice.copy()).to(dev)
+    V = torch.from_numpy(st.V.copy()).to(dev)
+    A = torch.from_numpy(st.A.copy()).to(dev)
+    ct = torch.from_numpy(np.ascontiguousarray(w.cell_type, dtype=np.uint8)).to(dev)
+    stream = torch.cuda.current_stream()
+    for call in range(2):
+        t, sp = st.t, st.sp
+        acc = ctypes.c_int64(-1)
+        rc = lib.cpm_step_noalloc(ctypes.byref(cfg), lat.data_ptr(), V.data_ptr(), A.data_ptr(), ct.data_ptr(),
+                                  t, sp, 5, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(acc))
+        assert rc == cpm.CPM_OK, rc
+        n_acc = st.replay_subpasses(5)
+        torch.cuda.synchronize()
+        assert np.array_equal(lat.cpu().numpy(), st.lattice), "lattice, call %d" % call
+        assert np.array_equal(V.cpu().numpy(), st.V), "V, call %d" % call
+        assert np.array_equal(A.cpu().numpy(), st.A), "A, call %d" % call
+        assert acc.value == n_acc, "accepts, call %d" % call
+
+
+def test_noalloc_refuses_a_capturing_stream(cpm):
+    """The call uploads its tables from host buffers that the next call
+    rewrites, so it refuses a stream under graph capture (CPM_E_INVALID)
+    before it queues any work."""
+    w = cw.point_cells_2d(seed=3, n=16, n_cells=4, a=4)
+    lib = cpm.load()
+    keep = []
+    cfg = cpm.make_config(w, keep)
+    dev = torch.device("cuda")
+    lat = torch.from_numpy(np.ascontiguousarray(w.lattice, dtype=np.int32)).to(dev)
+    V = torch.zeros(w.n_cells + 1, dtype=torch.int32, device=dev)
+    ct = torch.from_numpy(np.ascontiguousarray(w.cell_type, dtype=np.uint8)).to(dev)
+    x = torch.zeros(4, device=dev)
+    side = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        rc = lib.cpm_step_noalloc(ctypes.byref(cfg), lat.data_ptr(), V.data_ptr(), V.data_ptr(), ct.data_ptr(),
+                                  0, 0, 1, ctypes.c_void_p(side.cuda_stream), None)
+        x += 1
+    assert rc == cpm.CPM_E_INVALID
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(x.sum()) == 4.0
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(cpm):
     lib = cpm.load()
     dummy = torch.zeros(16, dtype=torch.int32, device="cuda")
@@ -96,3 +154,7 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(cpm):
     cfg.temperature = 20.0
     cfg.lambda_act[1] = 10
     assert lib.cpm_step_noalloc(ctypes.byref(cfg), p, p, p, p, 0, 0, 1, None, None) == cpm.CPM_E_LIMIT
+    cfg.lambda_act[1] = 0
+    # 2048^3 sites with 64^3 areas: few active blocks, but more than 2^31 sites
+    cfg.dim, cfg.nx, cfg.ny, cfg.nz, cfg.a, cfg.c, cfg.P = 3, 2048, 2048, 2048, 64, 2, 8
+    assert lib.cpm_step_noalloc(ctypes.byref(cfg), p, p, p, p, 0, 0, 1, None, None) == cpm.CPM_E_INVALID
