@@ -110,6 +110,10 @@ def lib():
         _lib.orc_neighbour_offsets.argtypes = [ctypes.c_int, i32p]
         _lib.orc_subpass_targets.argtypes = [P(Params), ctypes.c_int64, ctypes.c_int32, i64p]
         _lib.orc_subpass_targets.restype = ctypes.c_int64
+        _lib.orc_replay_trace.argtypes = [P(Params), i32p, u8p, i32p, i32p, i64p, i32p, ctypes.c_int64, i64p,
+                                          i64p, ctypes.c_int64, i64p]
+        _lib.orc_tile_offset_of.argtypes = [P(Params), ctypes.c_int64, i64p]
+        _lib.orc_tile_offset_of.restype = None
     return _lib
 
 
@@ -178,6 +182,25 @@ class State:
         self.t, self.sp = t.value, sp.value
         self.accepts += acc.value
         return acc.value
+
+    def replay_trace(self, n_sub: int) -> np.ndarray:
+        """replay_subpasses, returning the target site of every attempt in
+        the order the replay makes them (early rejects included)."""
+        t = ctypes.c_int64(self.t)
+        sp = ctypes.c_int32(self.sp)
+        acc = ctypes.c_int64(0)
+        n = ctypes.c_int64(0)
+        cap = int(n_sub) * self.w.n_sites // max(1, self.subpasses_per_mcs()) + self.w.n_sites
+        buf = np.zeros(cap, dtype=np.int64)
+        rc = lib().orc_replay_trace(ctypes.byref(self.params), _ptr(self.lattice, ctypes.c_int32),
+                                    _ptr(self.act, ctypes.c_uint8), _ptr(self.V, ctypes.c_int32),
+                                    _ptr(self.A, ctypes.c_int32), ctypes.byref(t), ctypes.byref(sp),
+                                    n_sub, ctypes.byref(acc), _ptr(buf, ctypes.c_int64), cap, ctypes.byref(n))
+        if rc != 0 or n.value > cap:
+            raise RuntimeError("orc_replay_trace failed: %d (%d attempts, room for %d)" % (rc, n.value, cap))
+        self.t, self.sp = t.value, sp.value
+        self.accepts += acc.value
+        return buf[:n.value].copy()
 
     def subpasses_per_mcs(self) -> int:
         """Schedule units per MCS: sub-passes (global rounds) or epochs (tiled)."""
@@ -319,6 +342,15 @@ def subpass_targets(w, t: int, sp: int) -> np.ndarray:
     out = np.zeros(w.n_sites, dtype=np.int64)
     n = lib().orc_subpass_targets(ctypes.byref(p), t, sp, _ptr(out, ctypes.c_int64))
     return out[:n].copy()
+
+
+def tile_offset(w, t: int) -> np.ndarray:
+    """Offset (x, y, z) of the tile grid of the tiled schedule in MCS t."""
+    ct = np.ascontiguousarray(w.cell_type, dtype=np.uint8)
+    p = make_params(w, ct)
+    off = np.zeros(3, dtype=np.int64)
+    lib().orc_tile_offset_of(ctypes.byref(p), t, _ptr(off, ctypes.c_int64))
+    return off
 
 
 def neighbour_offsets(dim: int) -> np.ndarray:

@@ -705,6 +705,19 @@ int64_t orc_subpass_targets(const orc_params *p, int64_t t, int32_t sp, int64_t 
     return cnt;
 }
 
+/* Optional record of the target site of every attempt, in the order the
+ * replay makes them (early rejects included); used by the schedule pins. */
+typedef struct {
+    int64_t *j;
+    int64_t n, cap;
+} orc_trace;
+
+static void trace_target(orc_trace *tr, int64_t j)
+{
+    if (tr && tr->n < tr->cap) tr->j[tr->n] = j;
+    if (tr) tr->n++;
+}
+
 /* Round r of sub-pass sp of MCS t over the listed blocks (all blocks of the
  * active colour when blocks == NULL).  Every attempt of the round reads the
  * tallies as they stood when the round began: the changes of all earlier
@@ -715,7 +728,7 @@ int64_t orc_subpass_targets(const orc_params *p, int64_t t, int32_t sp, int64_t 
  * block, so no attempt reads a site another attempt of the round writes. */
 static int replay_round(const orc_params *p, const orc_tables *tb, int32_t *lat, uint8_t *act,
                         int32_t *V, int32_t *A, int64_t t, int32_t sp, int r, const int64_t *blocks,
-                        int64_t n_blocks, int64_t *accepts)
+                        int64_t n_blocks, int64_t *accepts, orc_trace *tr)
 {
     int32_t off[26][3];
     int nb = orc_neighbour_offsets(p->dim, off);
@@ -747,6 +760,7 @@ static int replay_round(const orc_params *p, const orc_tables *tb, int32_t *lat,
         int n;
         uint32_t w2;
         attempt_draw(p, b, r, t, sp, &j, &n, &w2);
+        trace_target(tr, j);
         int64_t i = neighbour(p, j, off[n]);
         int32_t si = lat[i], sj = lat[j];
         if (si == sj || si < 0 || sj < 0) continue;
@@ -772,11 +786,11 @@ static int replay_round(const orc_params *p, const orc_tables *tb, int32_t *lat,
 
 /* all k = s^d / P rounds of one sub-pass */
 static int replay_subpass(const orc_params *p, const orc_tables *tb, int32_t *lat, uint8_t *act,
-                          int32_t *V, int32_t *A, int64_t t, int32_t sp, int64_t *accepts)
+                          int32_t *V, int32_t *A, int64_t t, int32_t sp, int64_t *accepts, orc_trace *tr)
 {
     int k = ipow(p->a / p->c, p->dim) / p->P;
     for (int r = 0; r < k; r++)
-        if (replay_round(p, tb, lat, act, V, A, t, sp, r, NULL, 0, accepts) != 0) return -1;
+        if (replay_round(p, tb, lat, act, V, A, t, sp, r, NULL, 0, accepts, tr) != 0) return -1;
     return 0;
 }
 
@@ -833,7 +847,7 @@ typedef struct {
 
 /* One epoch (tile cycle pc_t, tile colour number qt) of MCS t. */
 static int replay_epoch(const orc_params *p, const orc_tables *tb, int32_t *lat, uint8_t *act, int32_t *V,
-                        int32_t *A, int64_t t, int pc_t, int qt, int64_t *accepts)
+                        int32_t *A, int64_t t, int pc_t, int qt, int64_t *accepts, orc_trace *tr)
 {
     int32_t off[26][3];
     int nb = orc_neighbour_offsets(p->dim, off);
@@ -897,6 +911,7 @@ static int replay_epoch(const orc_params *p, const orc_tables *tb, int32_t *lat,
                                     int n;
                                     uint32_t w2;
                                     attempt_draw(p, b, r, t, sp, &j, &n, &w2);
+                                    trace_target(tr, j);
                                     int64_t i = neighbour(p, j, off[n]);
                                     int32_t si = lat[i], sj = lat[j];
                                     if (si == sj || si < 0 || sj < 0) continue;
@@ -969,8 +984,8 @@ static int check_params(const orc_params *p)
 /* Advance by n_sub schedule units (sub-passes of the global schedule,
  * epochs of the tiled one) from position (t, sp); Act decays at the start
  * of every MCS (sp == 0).  Position is updated in place. */
-int orc_replay_run(const orc_params *p, int32_t *lat, uint8_t *act, int32_t *V, int32_t *A,
-                   int64_t *t_io, int32_t *sp_io, int64_t n_sub, int64_t *accepts)
+static int replay_units(const orc_params *p, int32_t *lat, uint8_t *act, int32_t *V, int32_t *A,
+                        int64_t *t_io, int32_t *sp_io, int64_t n_sub, int64_t *accepts, orc_trace *tr)
 {
     if (check_params(p)) return -2;
     orc_tables tb;
@@ -983,8 +998,8 @@ int orc_replay_run(const orc_params *p, int32_t *lat, uint8_t *act, int32_t *V, 
     if (accepts) *accepts = 0;
     for (int64_t it = 0; it < n_sub; it++) {
         if (sp == 0 && use_act) decay_act(p, act);
-        int rc = p->tile ? replay_epoch(p, &tb, lat, act, V, A, t, sp / CT, sp % CT, accepts)
-                         : replay_subpass(p, &tb, lat, act, V, A, t, sp, accepts);
+        int rc = p->tile ? replay_epoch(p, &tb, lat, act, V, A, t, sp / CT, sp % CT, accepts, tr)
+                         : replay_subpass(p, &tb, lat, act, V, A, t, sp, accepts, tr);
         if (rc != 0) {
             tables_free(&tb);
             return -1;
@@ -1001,6 +1016,28 @@ int orc_replay_run(const orc_params *p, int32_t *lat, uint8_t *act, int32_t *V, 
     return 0;
 }
 
+int orc_replay_run(const orc_params *p, int32_t *lat, uint8_t *act, int32_t *V, int32_t *A,
+                   int64_t *t_io, int32_t *sp_io, int64_t n_sub, int64_t *accepts)
+{
+    return replay_units(p, lat, act, V, A, t_io, sp_io, n_sub, accepts, NULL);
+}
+
+/* As orc_replay_run, also writing the target site of every attempt, in
+ * replay order, to targets[0 .. cap-1]; *n_targets receives the number of
+ * attempts made (which may exceed cap). */
+int orc_replay_trace(const orc_params *p, int32_t *lat, uint8_t *act, int32_t *V, int32_t *A,
+                     int64_t *t_io, int32_t *sp_io, int64_t n_sub, int64_t *accepts, int64_t *targets,
+                     int64_t cap, int64_t *n_targets)
+{
+    orc_trace tr = {targets, 0, cap};
+    int rc = replay_units(p, lat, act, V, A, t_io, sp_io, n_sub, accepts, &tr);
+    *n_targets = tr.n;
+    return rc;
+}
+
+/* Offset of the tile grid in MCS t (tiled schedule), per axis. */
+void orc_tile_offset_of(const orc_params *p, int64_t t, int64_t off[3]) { tile_offset(p, t, off); }
+
 /* Round r of sub-pass sp of MCS t restricted to the given block indices
  * (others untouched); tallies are read from V and A as given; no Act decay
  * is applied here.  Used for sampled checks at full size. */
@@ -1012,7 +1049,7 @@ int orc_replay_round(const orc_params *p, int32_t *lat, uint8_t *act, int32_t *V
     orc_tables tb;
     if (tables_init(p, &tb) != 0) return -1;
     if (accepts) *accepts = 0;
-    int rc = replay_round(p, &tb, lat, act, V, A, t, sp, r, blocks, n_blocks, accepts);
+    int rc = replay_round(p, &tb, lat, act, V, A, t, sp, r, blocks, n_blocks, accepts, NULL);
     tables_free(&tb);
     return rc;
 }

@@ -252,3 +252,129 @@ def test_replay_block_subset_matches_full_subpass():
     part.replay_blocks(0, 3, 0, np.arange(nblk))
     assert np.array_equal(full.lattice, part.lattice)
     assert np.array_equal(full.V, part.V) and np.array_equal(full.A, part.A)
+
+
+# ---------------------------------------------------------------------------
+# the tiled schedule (tile = T > 0): tiles of edge T on a grid shifted per MCS,
+# 2^d tile colours, P_T tile cycles per MCS; in an epoch the tiles of one
+# colour run their share of the MCS's sub-passes while the others are dormant
+# ---------------------------------------------------------------------------
+
+def _tile_colour(coords, off, n, T):
+    """Tile colour (parity of the tile coordinates) of sites (x, y, z) for a
+    tile grid of edge T offset by off."""
+    col = np.zeros(len(coords[0]), dtype=np.int64)
+    for d, (x, o, L) in enumerate(zip(coords, off, n)):
+        col += (((x - o) % L) // T % 2) << d
+    return col
+
+
+@pytest.mark.parametrize("dim,n,T,P,PT", [(2, 32, 8, 4, 1), (2, 32, 8, 4, 2), (3, 16, 8, 8, 2)])
+def test_tiled_schedule_update_statistics(dim, n, T, P, PT):
+    """Per MCS: exactly s^d attempts in every block (so N in all), each site
+    the target of Binomial(s^d, 1/s^d) of them; every epoch's attempts lie in
+    tiles of one colour, each colour taking P_T epochs per MCS; the grid
+    offset is a multiple of a, uniform below T along each axis."""
+    a, c = 4, 2
+    s = a // c
+    sd = s ** dim
+    w = cw.random_small(2, dim=dim, n=n, n_cells=3, a=a, c=c, P=P).replace(tile=T, tile_cycles=PT)
+    st = oracle.State(w)
+    epochs = PT * 2 ** dim
+    n_mcs = 60 if dim == 2 else 16
+    shape = (w.nx, w.ny, w.nz)
+    counts = []
+    for t in range(n_mcs):
+        tg = st.replay_trace(epochs)
+        assert len(tg) == w.n_sites
+        cnt = np.bincount(tg, minlength=w.n_sites)
+        counts.append(cnt)
+        x, y, z = tg % w.nx, (tg // w.nx) % w.ny, tg // (w.nx * w.ny)
+        blk = x // s + (w.nx // s) * (y // s + (w.ny // s) * (z // s))
+        assert (np.bincount(blk, minlength=w.n_sites // sd) == sd).all()
+        off = oracle.tile_offset(w, t)
+        cols = _tile_colour((x, y, z)[:dim], off[:dim], shape[:dim], T).reshape(epochs, -1)
+        seen = []
+        for e in range(epochs):
+            assert len(np.unique(cols[e])) == 1, "epoch %d of MCS %d spans tile colours" % (e, t)
+            seen.append(int(cols[e][0]))
+        assert sorted(seen) == sorted(list(range(2 ** dim)) * PT)
+    counts = np.concatenate(counts)
+    kmax = min(sd, 5)
+    obs = np.array([(counts == k).sum() for k in range(kmax)] + [(counts >= kmax).sum()], dtype=float)
+    pk = [math.comb(sd, k) * (1 / sd) ** k * (1 - 1 / sd) ** (sd - k) for k in range(kmax)]
+    exp_ = np.array(pk + [1 - sum(pk)]) * len(counts)
+    keep = exp_ > 0
+    chi2 = ((obs[keep] - exp_[keep]) ** 2 / exp_[keep]).sum()
+    assert chi2 < 30.0, (obs, exp_)
+    offs = np.array([oracle.tile_offset(w, t)[:dim] for t in range(4000)])
+    assert (offs % a == 0).all() and (offs >= 0).all() and (offs < T).all()
+    for d in range(dim):
+        obs = np.bincount(offs[:, d] // a, minlength=T // a).astype(float)
+        chi2 = ((obs - 4000 / (T // a)) ** 2 / (4000 / (T // a))).sum()
+        assert chi2 < 25.0, (d, obs)
+
+
+def _cells_inside_tiles(dim, n, T, seed, act):
+    """A lattice whose cells sit in the middle of the tiles of MCS 0's tile
+    grid: in every tile two touching 3^d cells of random types, at least
+    five sites from every tile border."""
+    base = cw.random_small(seed, dim=dim, n=n, n_cells=1, edge=3, perimeter=True, act=act, a=4, c=2,
+                           P=4 if dim == 2 else 8)
+    off = oracle.tile_offset(base.replace(tile=T), 0)
+    rng = np.random.default_rng(seed)
+    lat = np.zeros((n,) * dim, dtype=np.int32)
+    nt = n // T
+    cid = 0
+    for tc in np.ndindex(*(nt,) * dim):
+        lo = [int(off[dim - 1 - k]) + tc[k] * T + T // 2 - 3 for k in range(dim)]  # (z, y, x) order
+        for part in range(2):
+            cid += 1
+            sl = [slice(0, 0)] * dim
+            for k in range(dim):
+                start = lo[k] + (3 if (part and k == dim - 1) else 0)
+                sl[k] = np.arange(start, start + 3) % n
+            lat[np.ix_(*sl)] = cid
+    ct = np.zeros(cid + 1, dtype=np.uint8)
+    ct[1:] = rng.integers(1, 3, size=cid)
+    actv = None
+    if act:
+        actv = np.where(lat > 0, rng.integers(0, 30, size=lat.shape), 0).astype(np.uint8)
+    lat_ = lat if dim == 3 else lat[None]
+    if actv is not None and dim == 2:
+        actv = actv[None]
+    vt = base.v_target.copy()
+    vt[1:3] = 10 if dim == 2 else 30
+    lv = base.lambda_v.copy()
+    lv[1:3] = 80
+    return base.replace(lattice=lat_, cell_type=ct, act=actv, v_target=vt, lambda_v=lv, T=18.0), off
+
+
+@pytest.mark.parametrize("dim,n,T,PT,act", [(2, 64, 16, 1, False), (2, 64, 16, 4, True), (3, 32, 16, 1, True),
+                                             (3, 32, 16, 8, False)])
+def test_tiled_replay_equals_global_for_cells_inside_tiles(dim, n, T, PT, act):
+    """The tiled schedule runs the global schedule's sub-passes, rounds and
+    Philox draws tile by tile.  When every cell lies inside one tile, far
+    from its borders, no attempt reads a site another tile changes and no
+    cell's tallies change in two tiles, so one MCS of the tiled replay must
+    equal one MCS of the global replay bit for bit (lattice, tallies, Act)."""
+    w, off = _cells_inside_tiles(dim, n, T, 40 + dim + PT, act)
+    g = oracle.State(w)
+    tl = oracle.State(w.replace(tile=T, tile_cycles=PT))
+    acc_g = g.replay_run(1)
+    acc_t = tl.replay_run(1)
+    assert acc_g > 20, "the check needs accepted copies"
+    # the premise held during the MCS: no cell came within two sites of a border of MCS 0's grid
+    lat = g.lattice.reshape((n,) * dim)
+    for k in range(dim):
+        o = int(off[dim - 1 - k])
+        pos = (np.arange(n) - o) % T
+        near = (pos < 2) | (pos >= T - 2)
+        sl = [slice(None)] * dim
+        sl[k] = near
+        assert (lat[tuple(sl)] <= 0).all()
+    assert acc_t == acc_g
+    assert np.array_equal(tl.lattice, g.lattice)
+    assert np.array_equal(tl.V, g.V) and np.array_equal(tl.A, g.A)
+    if act:
+        assert np.array_equal(tl.act, g.act)
