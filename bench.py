@@ -47,12 +47,17 @@ WORKLOADS = {
     # the same model on a lattice larger than L2, for DRAM counters
     "cpm3d_512": (lambda: cw.cube_cells_3d(seed=1, n=512, a=4, c=2, P=8), 8,
                   "3D 512^3, otherwise as cpm3d_256"),
-    "cpm3d_tissue_1024": (lambda: cw.fibre_tissue_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda"), 10,
+    "cpm3d_tissue_1024": (lambda: cw.fibre_tissue_3d(seed=1, n=1024, device="cuda", **cw.TISSUE_SCHEDULE), 10,
                           "3D tissue 1024^3 Moore-26 with a Voronoi-edge fibre mask (15% frozen), ~0.9M motile "
                           "cells, V_t=800, A_t=4639, Act lambda=200 Max=30, J(c,c)=20, J(c,m)=10, "
-                          "J(c,fibre)=40, lambda_V=25, lambda_P=0.2, T=20 (x5 integer scale); a=4, c=2, P=8"),
-    "cpm3d_tissue_512": (lambda: cw.fibre_tissue_3d(seed=1, n=512, a=4, c=2, P=8, device="cuda"), 10,
+                          "J(c,fibre)=40, lambda_V=25, lambda_P=0.2, T=20 (x5 integer scale); "
+                          "a={a}, c={c}, P={P} (the schedule that matches the serial chain within 2 percent)"
+                          .format(**cw.TISSUE_SCHEDULE)),
+    "cpm3d_tissue_512": (lambda: cw.fibre_tissue_3d(seed=1, n=512, device="cuda", **cw.TISSUE_SCHEDULE), 10,
                          "3D tissue 512^3, otherwise as cpm3d_tissue_1024"),
+    # the paper's smaller areas (4^3, 2x2x2 checkerboard): faster, but biased against the serial chain
+    "cpm3d_tissue_1024_a4": (lambda: cw.fibre_tissue_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda"), 10,
+                             "as cpm3d_tissue_1024 with a=4, c=2, P=8"),
     # the tissue workload under the tiled schedule (tiles of edge 16, one tile cycle per MCS)
     "cpm3d_tissue_1024_tiled": (lambda: cw.fibre_tissue_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda")
                                 .replace(tile=16, tile_cycles=1), 10,
@@ -94,7 +99,8 @@ SWEEP_METRIC = "sweep points/s at <=5% stat error"
 # Burn-in MCS before the warm-up steps: cells start as small seeds and grow
 # to their target volumes; the timed window is the tissue after growth (the
 # per-MCS cost settles after ~60 MCS on the 1024^3 tissue).
-BURN_IN = {"cpm2d_200": 50, "cpm3d_256": 50, "cpm3d_512": 50, "cpm3d_tissue_1024": 60, "cpm3d_tissue_512": 60}
+BURN_IN = {"cpm2d_200": 50, "cpm3d_256": 50, "cpm3d_512": 50, "cpm3d_tissue_1024": cw.TISSUE_BURN_IN,
+           "cpm3d_tissue_512": cw.TISSUE_BURN_IN}
 
 DEFAULT_WORKLOAD = "cpm3d_tissue_1024"
 

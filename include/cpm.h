@@ -108,7 +108,7 @@ typedef struct cpm_config {
     int32_t obstacle_type;       /* type of id -1 sites, 1..CPM_MAX_TYPES-1 */
     int32_t a, c, P;             /* area edge, divisions per axis, cycles per MCS */
     uint64_t seed;
-    int32_t n_cells;             /* cells have ids 1..n_cells */
+    int32_t n_cells;             /* cells have ids 1..n_cells; n_cells <= 2^23 - 1 */
     const uint8_t *cell_type;    /* host, n_cells + 1 entries; [0] must be 0 */
     const int32_t *init_lattice; /* host, nx*ny*nz ids in -1..n_cells */
     const uint8_t *init_act;     /* host, nx*ny*nz Act values or NULL (all 0) */
@@ -325,7 +325,7 @@ void cpm_batch_destroy(cpm_batch *b);
  *
  * It allocates nothing: all scratch (second tally buffer, pending-change
  * buffers, threshold/log/exp tables, accept counter) lives in one fixed
- * file-scope device array of about 8.8 MiB, present on every GPU that loads
+ * file-scope device array of about 9.2 MiB, present on every GPU that loads
  * the library until the process exits.  Limits, beyond which the call
  * returns CPM_E_LIMIT without doing anything: at most 262,144 active blocks
  * per round (nx*ny*nz / a^d), at most 65,535 cells, a threshold table of at

@@ -27,11 +27,13 @@ struct cpm_handle {
     uint32_t nbx = 1, nby = 1, nbz = 1, n_active = 0;
     bool perim = false, act = false;
     // device state
-    int32_t *lat = nullptr;
-    uint8_t *stamp = nullptr;
+    int32_t *lat = nullptr;        // lattice words: ids, with the Act stamps in the high byte when act
+    int32_t *stage = nullptr;      // staging for host reads and loads of packed words (lazily allocated)
+    uint64_t stage_n = 0;
     uint8_t *cell_type = nullptr;
     int32_t *tallies = nullptr;  // V0, A0, V1, A1, Vtmp, Atmp; each n_cells + 1
     int4 *pend = nullptr;        // two buffers of n_active
+    uint8_t *flags = nullptr;    // two buffers of n_active: pend entry valid
     uint32_t *thr = nullptr;
     int32_t *ln_tab = nullptr;
     int32_t *expq = nullptr;
@@ -114,8 +116,9 @@ int validate(const cpm_config *c)
     if (!(c->temperature > 0.0) || c->temperature > 2900.0)
         return fail(nullptr, CPM_E_INVALID, "temperature must be in (0, 2900]");
     if (c->obstacle_type < 1 || c->obstacle_type >= CPM_MAX_TYPES) return fail(nullptr, CPM_E_INVALID, "bad obstacle_type");
-    if (c->n_cells < 0 || c->n_cells > (1 << 30)) return fail(nullptr, CPM_E_INVALID, "bad n_cells");
-    if (c->tile > 0 && c->n_cells >= 0x0FFFFFFF) return fail(nullptr, CPM_E_INVALID, "tiled schedule: n_cells < 2^28 - 1");
+    // ids share the lattice word with the Act stamp: 24-bit two's complement
+    if (c->n_cells < 0 || c->n_cells > kMaxCellId)
+        return fail(nullptr, CPM_E_INVALID, "n_cells must be in 0..%d", (int)kMaxCellId);
     if (!c->cell_type || !c->init_lattice) return fail(nullptr, CPM_E_INVALID, "cell_type and init_lattice are required");
     if (c->cell_type[0] != 0) return fail(nullptr, CPM_E_INVALID, "cell_type[0] (medium) must be 0");
     for (int i = 1; i <= c->n_cells; i++)
@@ -211,7 +214,17 @@ int reset_tallies(cpm_handle *h)
     const size_t bytes = sizeof(int32_t) * (h->n_cells + 1);
     CUDA_TRY(h, cudaMemcpyAsync(V_buf(h, cur ^ 1), V_buf(h, cur), bytes, cudaMemcpyDeviceToDevice, h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(A_buf(h, cur ^ 1), A_buf(h, cur), bytes, cudaMemcpyDeviceToDevice, h->stream));
-    CUDA_TRY(h, cudaMemsetAsync(h->pend, 0, sizeof(int4) * 2 * (size_t)h->n_active, h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(h->flags, 0, 2 * (size_t)h->n_active, h->stream));
+    return CPM_OK;
+}
+
+// Staging buffer of up to 4 Mi words for host reads and loads of a packed lattice.
+int ensure_stage(cpm_handle *h)
+{
+    if (h->stage) return CPM_OK;
+    const uint64_t n = std::min<uint64_t>(h->n_sites, (uint64_t)1 << 22);
+    CUDA_TRY(h, cudaMalloc(&h->stage, sizeof(int32_t) * n));
+    h->stage_n = n;
     return CPM_OK;
 }
 
@@ -231,14 +244,14 @@ int pers_step(cpm_handle *h)
 int run_subpass(cpm_handle *h)
 {
     if (h->act && h->sp == 0 && h->t % 64 == 0) {
-        CUDA_TRY(h, launch_clamp_stamps(h->stamp, h->n_sites, (uint32_t)h->t, h->stream));
+        CUDA_TRY(h, launch_clamp_stamps(h->lat, h->n_sites, (uint32_t)h->t, h->stream));
         h->launches += 1;
     }
     const uint32_t col = colour_of(h, h->t, h->sp);
     RoundArgs a;
     memset(&a, 0, sizeof a);
     a.lat = h->lat;
-    a.stamp = h->stamp;
+    a.packed = h->act ? 1u : 0u;
     a.cell_type = h->cell_type;
     a.thr = h->thr;
     a.ln_tab = h->ln_tab;
@@ -270,6 +283,8 @@ int run_subpass(cpm_handle *h)
         a.An = A_buf(h, cur ^ 1);
         a.pend_prev = h->pend + (size_t)(cur ^ 1) * h->n_active;
         a.pend_cur = h->pend + (size_t)cur * h->n_active;
+        a.flag_prev = h->flags + (size_t)(cur ^ 1) * h->n_active;
+        a.flag_cur = h->flags + (size_t)cur * h->n_active;
         CUDA_TRY(h, launch_round(h->dim, h->perim, h->act, a, h->stream));
         h->launches += 1;
         h->g += 1;
@@ -312,7 +327,7 @@ uint32_t tile_colour_of(const cpm_handle *h, int64_t t, uint32_t cycle, uint32_t
 int run_epoch(cpm_handle *h)
 {
     if (h->act && h->sp == 0 && h->t % 64 == 0) {
-        CUDA_TRY(h, launch_clamp_stamps(h->stamp, h->n_sites, (uint32_t)h->t, h->stream));
+        CUDA_TRY(h, launch_clamp_stamps(h->lat, h->n_sites, (uint32_t)h->t, h->stream));
         h->launches += 1;
     }
     const uint32_t cycle = (uint32_t)h->sp / h->CT;
@@ -321,7 +336,6 @@ int run_epoch(cpm_handle *h)
     TileArgs a;
     memset(&a, 0, sizeof a);
     a.lat = h->lat;
-    a.stamp = h->stamp;
     a.cell_type = h->cell_type;
     const int cur = (int)(h->g & 1);
     a.Vc = V_buf(h, cur);
@@ -481,10 +495,11 @@ int build_tables(cpm_handle *h)
 void free_all(cpm_handle *h)
 {
     cudaFree(h->lat);
-    cudaFree(h->stamp);
+    cudaFree(h->stage);
     cudaFree(h->cell_type);
     cudaFree(h->tallies);
     cudaFree(h->pend);
+    cudaFree(h->flags);
     if (!h->shared_tables) {
         cudaFree(h->thr);
         cudaFree(h->ln_tab);
@@ -554,6 +569,7 @@ int create_impl(cpm_handle *h, const cpm_config *c, TableCache *cache = nullptr)
     CUDA_TRY(h, cudaMalloc(&h->cell_type, nv));
     CUDA_TRY(h, cudaMalloc(&h->tallies, sizeof(int32_t) * nv * 6));
     CUDA_TRY(h, cudaMalloc(&h->pend, sizeof(int4) * 2 * (size_t)h->n_active));
+    CUDA_TRY(h, cudaMalloc(&h->flags, 2 * (size_t)h->n_active));
     CUDA_TRY(h, cudaMalloc(&h->counters, sizeof(unsigned long long) * 2));
     if (h->tile) {
         CUDA_TRY(h, cudaMalloc(&h->error_flag, sizeof(int)));
@@ -574,9 +590,12 @@ int create_impl(cpm_handle *h, const cpm_config *c, TableCache *cache = nullptr)
             else
                 st[x] = (uint8_t)((c->t0 - 128) & 255);
         }
-        CUDA_TRY(h, cudaMalloc(&h->stamp, h->n_sites));
+        CUDA_TRY(h, cudaMalloc(&h->act_tmp, h->n_sites));
         // a copy from pageable memory returns once the source has been staged
-        CUDA_TRY(h, cudaMemcpyAsync(h->stamp, st.data(), h->n_sites, cudaMemcpyHostToDevice, h->stream));
+        CUDA_TRY(h, cudaMemcpyAsync(h->act_tmp, st.data(), h->n_sites, cudaMemcpyHostToDevice, h->stream));
+        // the stamps go into the high byte of the lattice words
+        CUDA_TRY(h, launch_pack_ids(h->lat, h->lat, h->act_tmp, h->n_sites, h->stream));
+        h->launches += 1;
     }
     int rc = cache ? build_tables_cached(h, cache) : build_tables(h);
     if (rc) return rc;
@@ -700,8 +719,22 @@ int cpm_read_lattice(cpm_handle *h, int32_t *dst, int dst_is_device)
     if (bad(h)) return CPM_E_HANDLE;
     if (!dst) return fail(h, CPM_E_INVALID, "dst is NULL");
     if (int rc = check_error_flag(h)) return rc;
-    CUDA_TRY(h, cudaMemcpyAsync(dst, h->lat, sizeof(int32_t) * h->n_sites,
-                                dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    if (!h->act) {
+        CUDA_TRY(h, cudaMemcpyAsync(dst, h->lat, sizeof(int32_t) * h->n_sites,
+                                    dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    } else if (dst_is_device) {
+        CUDA_TRY(h, launch_unpack_ids(h->lat, dst, h->n_sites, h->stream));
+        h->launches += 1;
+    } else {
+        // the ids of the packed words, chunk by chunk through the staging buffer
+        if (int rc = ensure_stage(h)) return rc;
+        for (uint64_t x = 0; x < h->n_sites; x += h->stage_n) {
+            const uint64_t m = std::min<uint64_t>(h->stage_n, h->n_sites - x);
+            CUDA_TRY(h, launch_unpack_ids(h->lat + x, h->stage, m, h->stream));
+            CUDA_TRY(h, cudaMemcpyAsync(dst + x, h->stage, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, h->stream));
+            h->launches += 1;
+        }
+    }
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return CPM_OK;
 }
@@ -748,7 +781,7 @@ int cpm_read_act(cpm_handle *h, uint8_t *dst, int dst_is_device)
     }
     if (!h->act_tmp) CUDA_TRY(h, cudaMalloc(&h->act_tmp, h->n_sites));
     const int64_t t_last = h->sp == 0 ? h->t - 1 : h->t;
-    CUDA_TRY(h, launch_act_values(h->lat, h->stamp, h->cell_type, h->tp, h->n_sites, (uint32_t)t_last, h->act_tmp,
+    CUDA_TRY(h, launch_act_values(h->lat, h->cell_type, h->tp, h->n_sites, (uint32_t)t_last, h->act_tmp,
                                   h->stream));
     h->launches += 1;
     CUDA_TRY(h, cudaMemcpyAsync(dst, h->act_tmp, h->n_sites, kind, h->stream));
@@ -760,8 +793,22 @@ int cpm_load_lattice(cpm_handle *h, const int32_t *src, int src_is_device)
 {
     if (bad(h)) return CPM_E_HANDLE;
     if (!src) return fail(h, CPM_E_INVALID, "src is NULL");
-    CUDA_TRY(h, cudaMemcpyAsync(h->lat, src, sizeof(int32_t) * h->n_sites,
-                                src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    if (!h->act) {
+        CUDA_TRY(h, cudaMemcpyAsync(h->lat, src, sizeof(int32_t) * h->n_sites,
+                                    src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    } else if (src_is_device) {
+        // new ids into the words, their Act stamps kept
+        CUDA_TRY(h, launch_pack_ids(h->lat, src, nullptr, h->n_sites, h->stream));
+        h->launches += 1;
+    } else {
+        if (int rc = ensure_stage(h)) return rc;
+        for (uint64_t x = 0; x < h->n_sites; x += h->stage_n) {
+            const uint64_t m = std::min<uint64_t>(h->stage_n, h->n_sites - x);
+            CUDA_TRY(h, cudaMemcpyAsync(h->stage, src + x, sizeof(int32_t) * m, cudaMemcpyHostToDevice, h->stream));
+            CUDA_TRY(h, launch_pack_ids(h->lat + x, h->stage, nullptr, m, h->stream));
+            h->launches += 1;
+        }
+    }
     return reset_tallies(h);
 }
 
@@ -1047,7 +1094,7 @@ int cpm_batch_create(const cpm_config *cfgs, int32_t n, void *cuda_stream, cpm_b
         memset(&L, 0, sizeof L);
         RoundArgs &a = L.base;
         a.lat = h->lat;
-        a.stamp = h->stamp;
+        a.packed = h->act ? 1u : 0u;
         a.cell_type = h->cell_type;
         a.thr = h->thr;
         a.ln_tab = h->ln_tab;
@@ -1067,6 +1114,7 @@ int cpm_batch_create(const cpm_config *cfgs, int32_t n, void *cuda_stream, cpm_b
             L.V[p] = V_buf(h, p);
             L.A[p] = A_buf(h, p);
             L.pend[p] = h->pend + (size_t)p * h->n_active;
+            L.flag[p] = h->flags + (size_t)p * h->n_active;
         }
         L.k = h->k;
         L.C = h->C;

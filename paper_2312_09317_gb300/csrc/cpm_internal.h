@@ -56,6 +56,19 @@ __host__ __device__ __forceinline__ uint32_t draw_below(uint32_t w, uint32_t n)
 #endif
 }
 
+// Lattice words.  With the Act term on, a site's word carries its cell id in
+// the low 24 bits (two's complement: -1 is a frozen obstacle) and its Act
+// time stamp (MCS mod 256 of its last update) in the high 8 bits, so that one
+// load gives both; without Act the word is the plain id.  Either way
+// cell_id() recovers the id (ids up to 2^23 - 1).
+constexpr int32_t kMaxCellId = (1 << 23) - 1;
+__host__ __device__ __forceinline__ int32_t cell_id(int32_t w) { return (int32_t)((uint32_t)w << 8) >> 8; }
+__host__ __device__ __forceinline__ uint32_t word_stamp(int32_t w) { return (uint32_t)w >> 24; }
+__host__ __device__ __forceinline__ int32_t pack_word(int32_t id, uint32_t stamp)
+{
+    return (int32_t)((stamp << 24) | ((uint32_t)id & 0x00FFFFFFu));
+}
+
 // Per-type model parameters, integer-scaled.
 struct TypeParams {
     int32_t J[kMaxTypes][kMaxTypes];
@@ -70,13 +83,15 @@ struct TypeParams {
 
 // Everything one round of the sweep needs.
 struct RoundArgs {
-    int32_t *lat;              // cell ids, x fastest
-    uint8_t *stamp;            // Act time stamps (MCS mod 256), or null
+    int32_t *lat;              // lattice words (see cell_id), x fastest
+    uint32_t packed;           // 1: the words carry Act stamps (Act on for this lattice)
     const uint8_t *cell_type;  // per cell id
     const int32_t *Vc, *Ac;    // tallies as of the start of this round
     int32_t *Vn, *An;          // tallies being built for the next round
-    const int4 *pend_prev;     // accepted change of the previous round, per active index
-    int4 *pend_cur;            // accepted change of this round, per active index
+    const int4 *pend_prev;     // accepted change of the previous round, per active index (valid where flagged)
+    int4 *pend_cur;            // accepted change of this round, per active index (written on accept only)
+    const uint8_t *flag_prev;  // 1 where the previous round accepted a copy, per active index
+    uint8_t *flag_cur;         // this round's flags (every active index written)
     const uint32_t *thr;       // acceptance thresholds, L entries
     const int32_t *ln_tab;     // LN[0..128]
     const int32_t *expq;       // EXPQ[m]
@@ -105,6 +120,7 @@ struct BatchLattice {
     RoundArgs base;
     int32_t *V[2], *A[2];
     int4 *pend[2];
+    uint8_t *flag[2];
     uint32_t R, k, C, pad_;
     int64_t t_start;
     uint64_t g_start;
@@ -149,8 +165,7 @@ constexpr uint32_t kTileHashCap = 512;  // distinct ids a tile and its halo may 
 constexpr uint32_t kTileThrSmem = 2048;  // threshold-table entries kept in shared memory
 
 struct TileArgs {
-    int32_t *lat;
-    uint8_t *stamp;
+    int32_t *lat;              // lattice words (see cell_id)
     const uint8_t *cell_type;
     const int32_t *Vc, *Ac;    // tallies at the start of the epoch (read-only during it)
     int32_t *Vn, *An;          // copy of Vc/Ac that receives every tile's changes
@@ -199,8 +214,12 @@ cudaError_t launch_recount(int dim, const int32_t *lat, const uint8_t *cell_type
                            uint32_t nx, uint32_t ny, uint32_t nz, cudaStream_t st);
 cudaError_t launch_compare(const int32_t *V, const int32_t *A, const int32_t *V2, const int32_t *A2, int32_t n,
                            unsigned long long *n_bad, cudaStream_t st);
-cudaError_t launch_clamp_stamps(uint8_t *stamp, uint64_t n, uint32_t t, cudaStream_t st);
-cudaError_t launch_act_values(const int32_t *lat, const uint8_t *stamp, const uint8_t *cell_type,
-                              const TypeParams &tp, uint64_t n, uint32_t t_last, uint8_t *out, cudaStream_t st);
+cudaError_t launch_clamp_stamps(int32_t *lat, uint64_t n, uint32_t t, cudaStream_t st);
+cudaError_t launch_act_values(const int32_t *lat, const uint8_t *cell_type, const TypeParams &tp, uint64_t n,
+                              uint32_t t_last, uint8_t *out, cudaStream_t st);
+// Lattice words <-> ids: unpack n words into ids; pack n ids into the words
+// of lat, keeping their stamps (or, with stamps != null, taking stamps[x]).
+cudaError_t launch_unpack_ids(const int32_t *lat, int32_t *ids, uint64_t n, cudaStream_t st);
+cudaError_t launch_pack_ids(int32_t *lat, const int32_t *ids, const uint8_t *stamps, uint64_t n, cudaStream_t st);
 
 }  // namespace cpmgb

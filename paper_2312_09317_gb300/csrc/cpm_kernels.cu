@@ -14,7 +14,9 @@
 // paper's atomic updates, Fig. 2B): round g reads buffer g&1 and adds both its
 // own accepted changes and those of round g-1 into buffer (g+1)&1, which then
 // equals the state after round g.  The change of round g-1 is carried in
-// pend_prev, indexed by active-block number (equal for every colour).
+// pend_prev, indexed by active-block number (equal for every colour); a
+// one-byte flag per active block says whether it holds a change, so that
+// only accepted copies (a few per cent) move a 16-byte entry.
 #include <cstdint>
 
 #include "cpm_internal.h"
@@ -60,9 +62,9 @@ __device__ __forceinline__ void around(uint32_t x, uint32_t n, uint32_t out[3])
 }
 
 // Act value of a site from its stamp: Max - age, clipped at 0.
-__device__ __forceinline__ int act_value(uint8_t stamp, uint32_t t8, int max_act)
+__device__ __forceinline__ int act_value(uint32_t stamp, uint32_t t8, int max_act)
 {
-    const int age = (int)((t8 - (uint32_t)stamp) & 255u);
+    const int age = (int)((t8 - stamp) & 255u);
     const int v = max_act - age;
     return v > 0 ? v : 0;
 }
@@ -91,8 +93,9 @@ __device__ int64_t gm_q(const RoundArgs &a, const SmemTables &sm, uint32_t x, ui
             for (int dx = 0; dx < 3; ++dx) {
                 const uint32_t site = xs[dx] + row;
                 const bool centre = dx == 1 && dy == 1 && dz == 1;
-                if (!centre && a.lat[site] != sigma) continue;
-                const int v = act_value(a.stamp[site], a.t & 255u, max_act);
+                const int32_t w = a.lat[site];
+                if (!centre && cell_id(w) != sigma) continue;
+                const int v = act_value(word_stamp(w), a.t & 255u, max_act);
                 if (v == 0) return 0;
                 sum += sm.ln[v];
                 cnt += 1;
@@ -167,8 +170,8 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
     constexpr int NB = DIM == 3 ? 26 : 8;
     bool accepted = false;
         // the previous round's accepted change goes into the next tallies
-        const int4 e = a.pend_prev[i];
-        if (e.x != e.y) {
+        if (a.flag_prev[i]) {
+            const int4 e = a.pend_prev[i];
             if (e.x > 0) { atomicAdd(a.Vn + e.x, 1); atomicAdd(a.An + e.x, e.z); }
             if (e.y > 0) { atomicAdd(a.Vn + e.y, -1); atomicAdd(a.An + e.y, e.w); }
         }
@@ -192,10 +195,9 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
         if (DIM == 3) around(jz, a.nz, zs); else zs[0] = zs[1] = zs[2] = 0;
         const uint32_t j = jx + a.nx * (jy + a.ny * jz);
         const uint32_t isite = xs[ox] + a.nx * (ys[oy] + a.ny * zs[oz]);
-        const int32_t sj = a.lat[j];
-        const int32_t si = a.lat[isite];
+        const int32_t sj = cell_id(a.lat[j]);
+        const int32_t si = cell_id(a.lat[isite]);
 
-        int4 out = make_int4(0, 0, 0, 0);
         if (si != sj && si >= 0 && sj >= 0) {
             const int32_t Vj = sj > 0 ? a.Vc[sj] : 0;
             if (!(sj > 0 && Vj <= 1)) {
@@ -211,7 +213,7 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
 #pragma unroll
                         for (int dx = 0; dx < 3; ++dx) {
                             if (dx == 1 && dy == 1 && dz == 1) continue;
-                            const int32_t sn = a.lat[xs[dx] + row];
+                            const int32_t sn = cell_id(a.lat[xs[dx] + row]);
                             const int tn = type_of(sn, a.cell_type, a.tp.obstacle_type);
                             if (sn != si) adhesion += sm.J[ti * kMaxTypes + tn]; else ++mi;
                             if (sn != sj) adhesion -= sm.J[tj * kMaxTypes + tn]; else ++mj;
@@ -274,16 +276,152 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
                 }
                 const bool ok = decided >= 0 ? decided == 1 : (dhq <= 0 || (dhq < a.L && w.v[2] < __ldg(a.thr + dhq)));
                 if (ok) {
-                    a.lat[j] = si;
-                    if (ACT && a.stamp) a.stamp[j] = (uint8_t)(si > 0 ? (a.t & 255u) : ((a.t - 128u) & 255u));
+                    // a copy stamps the site with this MCS (a medium copy: age 128, no activity)
+                    a.lat[j] = ACT && a.packed ? pack_word(si, si > 0 ? (a.t & 255u) : ((a.t - 128u) & 255u)) : si;
                     if (si > 0) { atomicAdd(a.Vn + si, 1); atomicAdd(a.An + si, dAi); }
                     if (sj > 0) { atomicAdd(a.Vn + sj, -1); atomicAdd(a.An + sj, dAj); }
-                    out = make_int4(si, sj, dAi, dAj);
+                    a.pend_cur[i] = make_int4(si, sj, dAi, dAj);
                     accepted = true;
                 }
             }
         }
-        a.pend_cur[i] = out;
+        a.flag_cur[i] = accepted ? 1 : 0;
+    return accepted;
+}
+
+// Act geometric mean (Q16) of a site from its 3x3x3 block of lattice words
+// (index dx + 3 dy + 9 dz, centre 13) already in registers: the same sites,
+// values and integer arithmetic as gm_q.
+__device__ __forceinline__ int64_t gm_words(const RoundArgs &a, const SmemTables &sm, const int32_t (&nbw)[27],
+                                            int32_t sigma, int max_act)
+{
+    if (sigma <= 0) return 0;
+    const uint32_t t8 = a.t & 255u;
+    int32_t sum = 0, cnt = 0;
+    bool zero = false;
+#pragma unroll
+    for (int k = 0; k < 27; ++k) {
+        const bool member = k == 13 || cell_id(nbw[k]) == sigma;
+        const int v = act_value(word_stamp(nbw[k]), t8, max_act);
+        if (member) {
+            zero |= v == 0;
+            sum += sm.ln[v];
+            cnt += 1;
+        }
+    }
+    return zero ? 0 : (int64_t)__ldg(a.expq + ((sum / cnt) >> 6));
+}
+
+// One copy attempt in 3D with the loads of each step issued together, so a
+// thread waits for memory about three times instead of once per load group:
+//   1. the target and source words (and the previous round's change flag);
+//   2. for a candidate copy (different ids, neither an obstacle): the other
+//      neighbours of the target and the tallies and types of both cells;
+//   3. types of third cells among the neighbours (rare), the energy change;
+//      with Act, the target's geometric mean from the words of step 2 and
+//      the source's from its own neighbourhood (mostly cached: it overlaps
+//      the target's).
+// Same draws, sums and decisions as round_attempt<3, ...>: the sums are of
+// integers and the geometric mean's sum and count do not depend on order.
+template <bool PERIM, bool ACT>
+__device__ __forceinline__ bool round_attempt3(const RoundArgs &a, const SmemTables &sm, uint32_t ix, uint32_t iy,
+                                               uint32_t iz, uint32_t i)
+{
+    constexpr int NB = 26;
+    const uint32_t bx = ix * a.c + a.cx, by = iy * a.c + a.cy, bz = iz * a.c + a.cz;
+    const uint32_t b = bx + a.nbx * (by + a.nby * bz);
+    const Philox4 w = philox4x32_10(b, a.r, a.t, a.sp, a.key0, a.key1);
+    const uint32_t jl = draw_below(w.v[0], a.sd);
+    const uint32_t jx = bx * a.s + jl % a.s;
+    const uint32_t jy = by * a.s + (jl / a.s) % a.s;
+    const uint32_t jz = bz * a.s + jl / (a.s * a.s);
+    const uint32_t n = draw_below(w.v[1], NB);
+    const uint32_t idx = n + (n >= NB / 2 ? 1u : 0u);  // skip the centre of the 3^3 stencil
+    const int ox = (int)(idx % 3), oy = (int)((idx / 3) % 3), oz = (int)(idx / 9);
+    uint32_t xs[3], ys[3], zs[3];
+    around(jx, a.nx, xs);
+    around(jy, a.ny, ys);
+    around(jz, a.nz, zs);
+    const uint32_t j = jx + a.nx * (jy + a.ny * jz);
+    const uint32_t isite = xs[ox] + a.nx * (ys[oy] + a.ny * zs[oz]);
+
+    // step 1
+    const int32_t wj = a.lat[j], wi = a.lat[isite];
+    if (a.flag_prev[i]) {
+        // the previous round's accepted change goes into the next tallies
+        const int4 e = a.pend_prev[i];
+        if (e.x > 0) { atomicAdd(a.Vn + e.x, 1); atomicAdd(a.An + e.x, e.z); }
+        if (e.y > 0) { atomicAdd(a.Vn + e.y, -1); atomicAdd(a.An + e.y, e.w); }
+    }
+    const int32_t sj = cell_id(wj), si = cell_id(wi);
+    bool accepted = false;
+    if (si != sj && si >= 0 && sj >= 0) {
+        // step 2
+        int32_t nbw[27];
+#pragma unroll
+        for (int k = 0; k < 27; ++k) {
+            const int dx = k % 3, dy = (k / 3) % 3, dz = k / 9;
+            nbw[k] = k == 13 ? wj : a.lat[xs[dx] + a.nx * (ys[dy] + a.ny * zs[dz])];
+        }
+        const int32_t Vj = sj > 0 ? a.Vc[sj] : 0;
+        const int64_t Vi = si > 0 ? a.Vc[si] : 0;
+        const int64_t Ai = PERIM && si > 0 ? a.Ac[si] : 0;
+        const int64_t Aj = PERIM && sj > 0 ? a.Ac[sj] : 0;
+        const int ti = type_of(si, a.cell_type, a.tp.obstacle_type);
+        const int tj = type_of(sj, a.cell_type, a.tp.obstacle_type);
+        if (!(sj > 0 && Vj <= 1)) {
+            // step 3
+            int32_t adhesion = 0;
+            int mi = 0, mj = 0;
+#pragma unroll
+            for (int k = 0; k < 27; ++k) {
+                if (k == 13) continue;
+                const int32_t sn = cell_id(nbw[k]);
+                const int tn = sn == si ? ti : (sn == sj ? tj : (sn == 0 ? 0 : type_of(sn, a.cell_type, a.tp.obstacle_type)));
+                if (sn != si) adhesion += sm.J[ti * kMaxTypes + tn]; else ++mi;
+                if (sn != sj) adhesion -= sm.J[tj * kMaxTypes + tn]; else ++mj;
+            }
+            const int dAi = NB - 2 * mi, dAj = 2 * mj - NB;
+            int64_t dh = adhesion;
+            if (si > 0) {
+                dh += (int64_t)sm.lv[ti] * (2 * (Vi - sm.vt[ti]) + 1);
+                if (PERIM) dh += (int64_t)sm.lp[ti] * dAi * (2 * (Ai - sm.at[ti]) + dAi);
+            }
+            if (sj > 0) {
+                dh += (int64_t)sm.lv[tj] * (1 - 2 * ((int64_t)Vj - sm.vt[tj]));
+                if (PERIM) dh += (int64_t)sm.lp[tj] * dAj * (2 * (Aj - sm.at[tj]) + dAj);
+            }
+            int64_t dhq = 16 * dh;
+            if (a.chem || a.pers_dir) dhq += motility_q<3>(a, si, sj, ti, tj, ox, oy, oz, isite);
+            int decided = -1;  // 1 accept, 0 reject, -1 open
+            if (ACT) {
+                const int tp = si > 0 ? ti : tj;
+                const int64_t lam = sm.la[tp], mx = sm.ma[tp];
+                if (lam != 0 && mx != 0) {
+                    // the Act term's range decides the test without the geometric means when it can
+                    const int64_t lo = dhq + floor_div_pos(-lam * (si > 0 ? a.tp.gm_max[ti] : 0), mx * 4096);
+                    const int64_t hi = dhq + floor_div_pos(lam * (sj > 0 ? a.tp.gm_max[tj] : 0), mx * 4096);
+                    if (hi <= 0) decided = 1;
+                    else if (lo >= a.L || (lo > 0 && w.v[2] >= __ldg(a.thr + lo))) decided = 0;
+                    else {
+                        const int64_t gj = gm_words(a, sm, nbw, sj, sj > 0 ? sm.ma[tj] : 0);
+                        const int64_t gi = gm_q<3, 1>(a, sm, xs[ox], ys[oy], zs[oz], si, si > 0 ? sm.ma[ti] : 0);
+                        dhq += floor_div_pos(lam * (gj - gi), mx * 4096);
+                    }
+                }
+            }
+            const bool ok = decided >= 0 ? decided == 1 : (dhq <= 0 || (dhq < a.L && w.v[2] < __ldg(a.thr + dhq)));
+            if (ok) {
+                // a copy stamps the site with this MCS (a medium copy: age 128, no activity)
+                a.lat[j] = ACT && a.packed ? pack_word(si, si > 0 ? (a.t & 255u) : ((a.t - 128u) & 255u)) : si;
+                if (si > 0) { atomicAdd(a.Vn + si, 1); atomicAdd(a.An + si, dAi); }
+                if (sj > 0) { atomicAdd(a.Vn + sj, -1); atomicAdd(a.An + sj, dAj); }
+                a.pend_cur[i] = make_int4(si, sj, dAi, dAj);
+                accepted = true;
+            }
+        }
+    }
+    a.flag_cur[i] = accepted ? 1 : 0;
     return accepted;
 }
 
@@ -299,9 +437,16 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
 #ifndef CPM_ROUND_MIN_BLOCKS_ACT
 #define CPM_ROUND_MIN_BLOCKS_ACT 8
 #endif
+// 3D (round_attempt3, CTAs of 128): the 26 neighbour words of a candidate are
+// held in registers, so the budget is 64 registers (eight CTAs per SM).
+#ifndef CPM_ROUND3_MIN_BLOCKS
+#define CPM_ROUND3_MIN_BLOCKS 8
+#endif
 
 template <int DIM, bool PERIM, bool ACT>
-__global__ void __launch_bounds__(kThreads, ACT ? CPM_ROUND_MIN_BLOCKS_ACT : CPM_ROUND_MIN_BLOCKS)
+__global__ void __launch_bounds__(DIM == 3 ? 128 : kThreads,
+                                  DIM == 3 ? CPM_ROUND3_MIN_BLOCKS
+                                           : (ACT ? CPM_ROUND_MIN_BLOCKS_ACT : CPM_ROUND_MIN_BLOCKS))
     round_kernel(const RoundArgs a)
 {
     __shared__ SmemTables sm;
@@ -322,7 +467,10 @@ __global__ void __launch_bounds__(kThreads, ACT ? CPM_ROUND_MIN_BLOCKS_ACT : CPM
     const uint32_t i = ix + a.nax * (iy + a.nay * iz);
     bool accepted = false;
     if (valid) {
-        accepted = round_attempt<DIM, PERIM, ACT, ACT ? 1 : 0>(a, sm, ix, iy, iz, i);
+        if (DIM == 3)
+            accepted = round_attempt3<PERIM, ACT>(a, sm, ix, iy, iz, i);
+        else
+            accepted = round_attempt<DIM, PERIM, ACT, ACT ? 1 : 0>(a, sm, ix, iy, iz, i);
     }
     const unsigned m = __ballot_sync(0xffffffffu, accepted);
     if ((threadIdx.x & 31) == 0 && m != 0) atomicAdd(a.accepts, (unsigned long long)__popc(m));
@@ -377,6 +525,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, ACT ? CPM_BATCH_MIN_BLOCKS_A
         ra.An = L.A[par ^ 1u];
         ra.pend_prev = L.pend[par ^ 1u];
         ra.pend_cur = L.pend[par];
+        ra.flag_prev = L.flag[par ^ 1u];
+        ra.flag_cur = L.flag[par];
     }
     __syncthreads();
     load_tables(sm, ra, ACT);
@@ -404,7 +554,7 @@ __global__ void recount_kernel(const int32_t *__restrict__ lat, int32_t *V, int3
                                uint32_t nz, uint64_t n)
 {
     for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
-        const int32_t s = lat[x];
+        const int32_t s = cell_id(lat[x]);
         if (s <= 0) continue;
         const uint32_t px = (uint32_t)(x % nx), py = (uint32_t)((x / nx) % ny), pz = (uint32_t)(x / ((uint64_t)nx * ny));
         uint32_t xs[3], ys[3], zs[3];
@@ -416,7 +566,7 @@ __global__ void recount_kernel(const int32_t *__restrict__ lat, int32_t *V, int3
             for (int dy = 0; dy < 3; ++dy)
                 for (int dx = 0; dx < 3; ++dx) {
                     if (dx == 1 && dy == 1 && dz == 1) continue;
-                    cnt += lat[xs[dx] + nx * (ys[dy] + ny * zs[dz])] != s;
+                    cnt += cell_id(lat[xs[dx] + nx * (ys[dy] + ny * zs[dz])]) != s;
                 }
         atomicAdd(V + s, 1);
         atomicAdd(A + s, cnt);
@@ -431,25 +581,45 @@ __global__ void compare_kernel(const int32_t *V, const int32_t *A, const int32_t
 }
 
 // Stamps whose age is 128 or more are reset to age exactly 128, so that ages
-// stay below 256 until the next clamp (run every 64 MCS).
-__global__ void clamp_kernel(uint8_t *stamp, uint64_t n, uint32_t t)
+// stay below 256 until the next clamp (run every 64 MCS).  Obstacle words are
+// left as they are (their stamp is never read).
+__device__ __forceinline__ void clamp_word(int32_t *p, uint32_t t8)
+{
+    const int32_t w = *p;
+    if (cell_id(w) < 0) return;
+    const uint32_t age = (t8 - word_stamp(w)) & 255u;
+    if (age >= 128u) *p = pack_word(cell_id(w), (t8 - 128u) & 255u);
+}
+
+__global__ void clamp_kernel(int32_t *lat, uint64_t n, uint32_t t)
 {
     const uint32_t t8 = t & 255u;
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x)
+        clamp_word(lat + x, t8);
+}
+
+__global__ void act_values_kernel(const int32_t *lat, const uint8_t *cell_type, TypeParams tp, uint64_t n,
+                                  uint32_t t_last, uint8_t *out)
+{
     for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t age = (t8 - (uint32_t)stamp[x]) & 255u;
-        if (age >= 128u) stamp[x] = (uint8_t)((t8 - 128u) & 255u);
+        const int32_t w = lat[x];
+        const int32_t s = cell_id(w);
+        int v = 0;
+        if (s > 0) v = act_value(word_stamp(w), t_last & 255u, tp.max_act[cell_type[s]]);
+        out[x] = (uint8_t)v;
     }
 }
 
-__global__ void act_values_kernel(const int32_t *lat, const uint8_t *stamp, const uint8_t *cell_type, TypeParams tp,
-                                  uint64_t n, uint32_t t_last, uint8_t *out)
+__global__ void unpack_ids_kernel(const int32_t *lat, int32_t *ids, uint64_t n)
 {
-    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
-        const int32_t s = lat[x];
-        int v = 0;
-        if (s > 0) v = act_value(stamp[x], t_last & 255u, tp.max_act[cell_type[s]]);
-        out[x] = (uint8_t)v;
-    }
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x)
+        ids[x] = cell_id(lat[x]);
+}
+
+__global__ void pack_ids_kernel(int32_t *lat, const int32_t *ids, const uint8_t *stamps, uint64_t n)
+{
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x)
+        lat[x] = pack_word(ids[x], stamps ? (uint32_t)stamps[x] : word_stamp(lat[x]));
 }
 
 unsigned grid_for(uint64_t n, unsigned threads)
@@ -489,14 +659,11 @@ __global__ void batch_clamp_kernel(const BatchLattice *lats, const int2 *items)
 {
     const int2 it = items[blockIdx.x];
     const BatchLattice &L = lats[it.x];
-    if (L.base.stamp == nullptr || (L.t_start % 64) != 0) return;
+    if (!L.base.packed || (L.t_start % 64) != 0) return;
     const uint64_t n = (uint64_t)L.base.nx * L.base.ny * L.base.nz;
     const uint32_t t8 = (uint32_t)L.t_start & 255u;
     const uint64_t lo = (uint64_t)it.y * 65536u, hi = lo + 65536u < n ? lo + 65536u : n;
-    for (uint64_t x = lo + threadIdx.x; x < hi; x += blockDim.x) {
-        const uint32_t age = (t8 - (uint32_t)L.base.stamp[x]) & 255u;
-        if (age >= 128u) L.base.stamp[x] = (uint8_t)((t8 - 128u) & 255u);
-    }
+    for (uint64_t x = lo + threadIdx.x; x < hi; x += blockDim.x) clamp_word(L.base.lat + x, t8);
 }
 
 // End of one batch MCS: every member moves to its next MCS.
@@ -564,16 +731,30 @@ cudaError_t launch_compare(const int32_t *V, const int32_t *A, const int32_t *V2
     return cudaGetLastError();
 }
 
-cudaError_t launch_clamp_stamps(uint8_t *stamp, uint64_t n, uint32_t t, cudaStream_t st)
+cudaError_t launch_clamp_stamps(int32_t *lat, uint64_t n, uint32_t t, cudaStream_t st)
 {
-    clamp_kernel<<<grid_for(n, 256), 256, 0, st>>>(stamp, n, t);
+    clamp_kernel<<<grid_for(n, 256), 256, 0, st>>>(lat, n, t);
     return cudaGetLastError();
 }
 
-cudaError_t launch_act_values(const int32_t *lat, const uint8_t *stamp, const uint8_t *cell_type, const TypeParams &tp,
-                              uint64_t n, uint32_t t_last, uint8_t *out, cudaStream_t st)
+cudaError_t launch_act_values(const int32_t *lat, const uint8_t *cell_type, const TypeParams &tp, uint64_t n,
+                              uint32_t t_last, uint8_t *out, cudaStream_t st)
 {
-    act_values_kernel<<<grid_for(n, 256), 256, 0, st>>>(lat, stamp, cell_type, tp, n, t_last, out);
+    act_values_kernel<<<grid_for(n, 256), 256, 0, st>>>(lat, cell_type, tp, n, t_last, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_ids(const int32_t *lat, int32_t *ids, uint64_t n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    unpack_ids_kernel<<<grid_for(n, 256), 256, 0, st>>>(lat, ids, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_ids(int32_t *lat, const int32_t *ids, const uint8_t *stamps, uint64_t n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    pack_ids_kernel<<<grid_for(n, 256), 256, 0, st>>>(lat, ids, stamps, n);
     return cudaGetLastError();
 }
 

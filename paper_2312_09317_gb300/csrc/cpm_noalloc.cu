@@ -28,12 +28,14 @@ constexpr int32_t kNaMaxThr = 32768;        // threshold table entries (T <= 92)
 constexpr int32_t kNaMaxExpq = 5120;
 
 constexpr size_t kPendBytes = sizeof(int4) * 2 * (size_t)kNaMaxActive;
+constexpr size_t kFlagBytes = 2 * (size_t)kNaMaxActive;
 constexpr size_t kTallyBytes = sizeof(int32_t) * 2 * ((size_t)kNaMaxCells + 1);
 constexpr size_t kThrBytes = sizeof(uint32_t) * (size_t)kNaMaxThr;
 constexpr size_t kLnBytes = 1024;
 constexpr size_t kExpqBytes = sizeof(int32_t) * (size_t)kNaMaxExpq;
 constexpr size_t kOffPend = 0;
-constexpr size_t kOffTally = kOffPend + kPendBytes;
+constexpr size_t kOffFlag = kOffPend + kPendBytes;
+constexpr size_t kOffTally = kOffFlag + kFlagBytes;
 constexpr size_t kOffThr = kOffTally + kTallyBytes;
 constexpr size_t kOffLn = kOffThr + kThrBytes;
 constexpr size_t kOffExpq = kOffLn + kLnBytes;
@@ -144,6 +146,7 @@ extern "C" int cpm_step_noalloc(const cpm_config *cfg, int32_t *lattice, int32_t
     int rc = scratch_for_current_device(&scr);
     if (rc) return rc;
     int4 *pend = (int4 *)(scr + kOffPend);
+    uint8_t *flags = scr + kOffFlag;
     int32_t *V1 = (int32_t *)(scr + kOffTally);
     int32_t *A1 = V1 + (kNaMaxCells + 1);
     uint32_t *d_thr = (uint32_t *)(scr + kOffThr);
@@ -173,7 +176,7 @@ extern "C" int cpm_step_noalloc(const cpm_config *cfg, int32_t *lattice, int32_t
         NA_TRY(cudaMemcpyAsync(d_ln, g_ln, sizeof g_ln, cudaMemcpyHostToDevice, st));
         NA_TRY(cudaMemcpyAsync(d_expq, g_expq, sizeof(int32_t) * (size_t)ne, cudaMemcpyHostToDevice, st));
     }
-    NA_TRY(cudaMemsetAsync(pend, 0, sizeof(int4) * 2 * (size_t)n_active, st));
+    NA_TRY(cudaMemsetAsync(flags, 0, 2 * (size_t)n_active, st));
     NA_TRY(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), st));
     NA_TRY(cudaMemcpyAsync(V1, V, tb, cudaMemcpyDeviceToDevice, st));
     NA_TRY(cudaMemcpyAsync(A1, A, tb, cudaMemcpyDeviceToDevice, st));
@@ -181,7 +184,7 @@ extern "C" int cpm_step_noalloc(const cpm_config *cfg, int32_t *lattice, int32_t
     RoundArgs a;
     memset(&a, 0, sizeof a);
     a.lat = lattice;
-    a.stamp = nullptr;
+    a.packed = 0;  // no Act term here: the words are plain ids
     a.cell_type = cell_type;
     a.thr = d_thr;
     a.ln_tab = d_ln;
@@ -238,6 +241,8 @@ extern "C" int cpm_step_noalloc(const cpm_config *cfg, int32_t *lattice, int32_t
             a.An = Ab[cur ^ 1];
             a.pend_prev = pend + (size_t)(cur ^ 1) * n_active;
             a.pend_cur = pend + (size_t)cur * n_active;
+            a.flag_prev = flags + (size_t)(cur ^ 1) * n_active;
+            a.flag_cur = flags + (size_t)cur * n_active;
             NA_TRY(launch_round(c.dim, perim, false, a, st));
         }
         if (++sp == (int32_t)per_mcs) {

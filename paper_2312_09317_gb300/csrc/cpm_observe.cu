@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kObsThreads) observe_anchor_kernel(const Obser
     const int lane = threadIdx.x & 31;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = base + threadIdx.x;
-        int id = i < n ? it.lat[i] : 0;
+        int id = i < n ? cell_id(it.lat[i]) : 0;
         if (id > it.n_cells) id = 0;  // never present in a validated lattice; keeps the write in bounds
         const unsigned grp = __match_any_sync(0xffffffffu, id);
         const unsigned lo = __reduce_min_sync(grp, (unsigned)(i < n ? i : 0xffffffffu));
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kObsThreads) observe_sums_kernel(const Observe
     const int lane = threadIdx.x & 31;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = base + threadIdx.x;
-        int id = i < n ? it.lat[i] : 0;
+        int id = i < n ? cell_id(it.lat[i]) : 0;
         if (id > it.n_cells) id = 0;
         int ox = 0, oy = 0, oz = 0, iface = 0, medium = 0;
         if (id > 0) {
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kObsThreads) observe_sums_kernel(const Observe
                         if (dx == 0 && dy == 0 && dz == 0) continue;
                         int xx = x + dx;
                         xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
-                        const int v = it.lat[(int64_t)zz * plane + (int64_t)yy * nx + xx];
+                        const int v = cell_id(it.lat[(int64_t)zz * plane + (int64_t)yy * nx + xx]);
                         iface += v != id;
                         medium += v == 0;
                     }

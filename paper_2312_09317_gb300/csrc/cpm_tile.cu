@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kTileThreads) tile_epoch_kernel(const TileArgs
 #pragma unroll
         for (int u = 0; u < kStage; ++u) {
             const uint32_t l = base + u * blockDim.x + threadIdx.x;
-            v[u] = l < n_local ? __ldg(a.lat + global_of(l)) : 0;
+            v[u] = l < n_local ? cell_id(__ldg(a.lat + global_of(l))) : 0;
         }
         int32_t last = 0;
 #pragma unroll
@@ -228,8 +228,9 @@ __global__ void __launch_bounds__(kTileThreads) tile_epoch_kernel(const TileArgs
             v[u] = 0;
             if (l < n_local) {
                 const uint64_t g = global_of(l);
-                v[u] = __ldcs(a.lat + g);
-                if (ACT) st[u] = a.stamp[g];
+                const int32_t w = __ldcs(a.lat + g);
+                v[u] = cell_id(w);
+                if (ACT) st[u] = (uint8_t)word_stamp(w);
             }
         }
 #pragma unroll
@@ -421,8 +422,8 @@ __global__ void __launch_bounds__(kTileThreads) tile_epoch_kernel(const TileArgs
         const uint32_t gx = (ox + lx) % a.nx, gy = (oy + ly) % a.ny, gz = DIM == 3 ? (oz + lz) % a.nz : 0;
         const uint64_t g = gx + (uint64_t)a.nx * (gy + (uint64_t)a.ny * gz);
         const uint32_t s_ = (lx + H) + W * ((ly + H) + W * (DIM == 3 ? lz + H : 0));
-        a.lat[g] = L.gid[slot_of(L.lat[s_])];
-        if (ACT) a.stamp[g] = L.stamp[s_];
+        const int32_t id = L.gid[slot_of(L.lat[s_])];
+        a.lat[g] = ACT ? pack_word(id, L.stamp[s_]) : id;
     }
     for (uint32_t sl = 2 + threadIdx.x; sl < ns; sl += blockDim.x) {
         const int32_t g = L.gid[sl];

@@ -1,0 +1,63 @@
+"""Writes tissue_serial_stats_128.json: the statistics of tests/tissue_stats.py
+for the serial CPM chain (oracle (a): Methods, Eq. 1-3, Eq. 8-9, one
+uniformly drawn attempt at a time) on the 128^3 Act fibre tissue, one entry
+per seed.  Calls only the oracle and the seeded input generators; the GPU
+test compares the parallel scheme's 64-seed means with these.
+
+    python tests/golden/make_tissue_serial_stats.py [n_procs]
+
+About 4 CPU-hours (64 seeds x 500 MCS x 2.1 M attempts)."""
+import json
+import multiprocessing as mp
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.dirname(HERE))
+
+SEEDS = list(range(1, 65))
+OUT = os.path.join(HERE, "tissue_serial_stats_128.json")
+
+
+def run(seed):
+    import torch
+    torch.set_num_threads(1)
+    import cpm_workloads as cw
+    import oracle
+    import tissue_stats as ts
+    w = cw.fibre_tissue_3d(seed=seed, n=ts.N)
+    st = oracle.State(w)
+    st.serial_run(ts.BURN)
+    rec = ts.Recorder((w.nz, w.ny, w.nx), w.n_cells)
+    shape = (w.nz, w.ny, w.nx)
+    rec.snapshot(torch.from_numpy(st.lattice.reshape(shape)))
+    acc = 0
+    for _ in range(ts.SNAPS):
+        acc += st.serial_run(ts.EVERY)
+        rec.snapshot(torch.from_numpy(st.lattice.reshape(shape)), st.V, st.A)
+    return seed, rec.summary(acc, w.n_sites)
+
+
+def main():
+    n_procs = int(sys.argv[1]) if len(sys.argv) > 1 else os.cpu_count()
+    t0 = time.time()
+    with mp.get_context("spawn").Pool(n_procs) as pool:
+        res = dict(pool.map(run, SEEDS))
+    import tissue_stats as ts
+    doc = {
+        "what": "serial CPM chain (oracle (a)) statistics of the 128^3 Act fibre tissue, per seed",
+        "protocol": {"n": ts.N, "burn_mcs": ts.BURN, "snapshots": ts.SNAPS, "every_mcs": ts.EVERY},
+        "seeds": SEEDS,
+        "stats": {k: [res[s][k] for s in SEEDS] for k in ts.STATS},
+        "cpu_seconds": round((time.time() - t0) * n_procs),
+    }
+    with open(OUT, "w") as f:
+        json.dump(doc, f, indent=1)
+    print("wrote", OUT, "in %.0f s" % (time.time() - t0))
+
+
+if __name__ == "__main__":
+    main()

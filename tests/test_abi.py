@@ -70,6 +70,7 @@ def _create(w, **over):
     ("temperature", 1e6, "temperature"),
     ("obstacle_type", 0, "obstacle_type"),
     ("n_cells", -1, "n_cells"),
+    ("n_cells", 1 << 23, "n_cells"),  # ids share the lattice word with the Act stamp: 24 bits
     ("t0", -5, "t0"),
 ])
 def test_invalid_configs_are_rejected_without_a_gpu(lib, field, value, msg):

@@ -213,12 +213,13 @@ def test_tissue_64_bit_exact(cpm):
 
 def test_tissue_1024_sampled(cpm):
     """1024^3 tissue workload in the launch configuration bench.py times
-    (a=4, c=2, P=8: one round per sub-pass).  After 2 MCS and 3 sub-passes,
+    (cpm_workloads.TISSUE_SCHEDULE: one round per sub-pass).  After 2 MCS and 3 sub-passes,
     one more round runs on the GPU; the oracle replays that round for 4,096
     sampled active blocks from the GPU's state before it, and their sites and
     Act values must match.  Tallies are checked at full size by a device
     recount, obstacles by comparison with the input."""
-    w = cw.fibre_tissue_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda")
+    w = cw.fibre_tissue_3d(seed=1, n=1024, device="cuda", **cw.TISSUE_SCHEDULE)
+    assert (w.a // w.c) ** 3 // w.P == 1  # one round per sub-pass: the sampled round is the whole sub-pass
     sim = cpm.Sim(w)
     sim.step(2)
     sim.step_subpasses(3)
