@@ -128,6 +128,18 @@ uint64_t cpm_mlp_kernel_launches(const cpm_mlp *h);
 const char *cpm_mlp_last_error(const cpm_mlp *h);
 int cpm_mlp_destroy(cpm_mlp *h);
 
+/* Test hook for the failure path of the tensor-core GEMM (the paper has no
+ * counterpart).  The GEMM waits for its tensor-core accumulator on an
+ * mbarrier with a bounded number of polls; when the bound runs out, the
+ * kernel records the timeout, waits (bounded) for the MMAs it issued, frees
+ * its tensor memory and returns, and the call that launched it returns
+ * CPM_MLP_E_CUDA with the message "tensor-core accumulator wait timed out".
+ * A healthy GPU never gets there, so this call arms the handle's next
+ * tensor-core GEMM launch to take that path after its wait has completed:
+ * the kernel reports the timeout and the handle stays usable for the calls
+ * after it.  Returns CPM_MLP_OK, or CPM_MLP_E_INVALID for a NULL handle. */
+int cpm_mlp_report_next_tc_timeout(cpm_mlp *h);
+
 /* The batched GEMM behind the network, exposed for tests:
  *   C[z][m][n] = epilogue( sum_k op(A)[m][k] op(B)[k][n] ),  z < batch,
  *   op(A)[m][k] = trans_a ? A[z*stride_a + k*lda + m] : A[z*stride_a + m*lda + k],

@@ -117,6 +117,7 @@ _SIGNATURES.update({
     "cpm_mlp_kernel_launches": (ctypes.c_uint64, [_VP]),
     "cpm_mlp_last_error": (ctypes.c_char_p, [_VP]),
     "cpm_mlp_destroy": (ctypes.c_int, [_VP]),
+    "cpm_mlp_report_next_tc_timeout": (ctypes.c_int, [_VP]),
     "cpm_mlp_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     _VP, _I64, _I64, _VP, _I64, _I64, _VP, _I64, _VP, ctypes.c_int, _I64, _I64,
                                     _VP, _I64, _I64, ctypes.c_int, _VP]),

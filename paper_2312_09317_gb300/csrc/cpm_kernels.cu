@@ -289,142 +289,6 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
     return accepted;
 }
 
-// Act geometric mean (Q16) of a site from its 3x3x3 block of lattice words
-// (index dx + 3 dy + 9 dz, centre 13) already in registers: the same sites,
-// values and integer arithmetic as gm_q.
-__device__ __forceinline__ int64_t gm_words(const RoundArgs &a, const SmemTables &sm, const int32_t (&nbw)[27],
-                                            int32_t sigma, int max_act)
-{
-    if (sigma <= 0) return 0;
-    const uint32_t t8 = a.t & 255u;
-    int32_t sum = 0, cnt = 0;
-    bool zero = false;
-#pragma unroll
-    for (int k = 0; k < 27; ++k) {
-        const bool member = k == 13 || cell_id(nbw[k]) == sigma;
-        const int v = act_value(word_stamp(nbw[k]), t8, max_act);
-        if (member) {
-            zero |= v == 0;
-            sum += sm.ln[v];
-            cnt += 1;
-        }
-    }
-    return zero ? 0 : (int64_t)__ldg(a.expq + ((sum / cnt) >> 6));
-}
-
-// One copy attempt in 3D with the loads of each step issued together, so a
-// thread waits for memory about three times instead of once per load group:
-//   1. the target and source words (and the previous round's change flag);
-//   2. for a candidate copy (different ids, neither an obstacle): the other
-//      neighbours of the target and the tallies and types of both cells;
-//   3. types of third cells among the neighbours (rare), the energy change;
-//      with Act, the target's geometric mean from the words of step 2 and
-//      the source's from its own neighbourhood (mostly cached: it overlaps
-//      the target's).
-// Same draws, sums and decisions as round_attempt<3, ...>: the sums are of
-// integers and the geometric mean's sum and count do not depend on order.
-template <bool PERIM, bool ACT>
-__device__ __forceinline__ bool round_attempt3(const RoundArgs &a, const SmemTables &sm, uint32_t ix, uint32_t iy,
-                                               uint32_t iz, uint32_t i)
-{
-    constexpr int NB = 26;
-    const uint32_t bx = ix * a.c + a.cx, by = iy * a.c + a.cy, bz = iz * a.c + a.cz;
-    const uint32_t b = bx + a.nbx * (by + a.nby * bz);
-    const Philox4 w = philox4x32_10(b, a.r, a.t, a.sp, a.key0, a.key1);
-    const uint32_t jl = draw_below(w.v[0], a.sd);
-    const uint32_t jx = bx * a.s + jl % a.s;
-    const uint32_t jy = by * a.s + (jl / a.s) % a.s;
-    const uint32_t jz = bz * a.s + jl / (a.s * a.s);
-    const uint32_t n = draw_below(w.v[1], NB);
-    const uint32_t idx = n + (n >= NB / 2 ? 1u : 0u);  // skip the centre of the 3^3 stencil
-    const int ox = (int)(idx % 3), oy = (int)((idx / 3) % 3), oz = (int)(idx / 9);
-    uint32_t xs[3], ys[3], zs[3];
-    around(jx, a.nx, xs);
-    around(jy, a.ny, ys);
-    around(jz, a.nz, zs);
-    const uint32_t j = jx + a.nx * (jy + a.ny * jz);
-    const uint32_t isite = xs[ox] + a.nx * (ys[oy] + a.ny * zs[oz]);
-
-    // step 1
-    const int32_t wj = a.lat[j], wi = a.lat[isite];
-    if (a.flag_prev[i]) {
-        // the previous round's accepted change goes into the next tallies
-        const int4 e = a.pend_prev[i];
-        if (e.x > 0) { atomicAdd(a.Vn + e.x, 1); atomicAdd(a.An + e.x, e.z); }
-        if (e.y > 0) { atomicAdd(a.Vn + e.y, -1); atomicAdd(a.An + e.y, e.w); }
-    }
-    const int32_t sj = cell_id(wj), si = cell_id(wi);
-    bool accepted = false;
-    if (si != sj && si >= 0 && sj >= 0) {
-        // step 2
-        int32_t nbw[27];
-#pragma unroll
-        for (int k = 0; k < 27; ++k) {
-            const int dx = k % 3, dy = (k / 3) % 3, dz = k / 9;
-            nbw[k] = k == 13 ? wj : a.lat[xs[dx] + a.nx * (ys[dy] + a.ny * zs[dz])];
-        }
-        const int32_t Vj = sj > 0 ? a.Vc[sj] : 0;
-        const int64_t Vi = si > 0 ? a.Vc[si] : 0;
-        const int64_t Ai = PERIM && si > 0 ? a.Ac[si] : 0;
-        const int64_t Aj = PERIM && sj > 0 ? a.Ac[sj] : 0;
-        const int ti = type_of(si, a.cell_type, a.tp.obstacle_type);
-        const int tj = type_of(sj, a.cell_type, a.tp.obstacle_type);
-        if (!(sj > 0 && Vj <= 1)) {
-            // step 3
-            int32_t adhesion = 0;
-            int mi = 0, mj = 0;
-#pragma unroll
-            for (int k = 0; k < 27; ++k) {
-                if (k == 13) continue;
-                const int32_t sn = cell_id(nbw[k]);
-                const int tn = sn == si ? ti : (sn == sj ? tj : (sn == 0 ? 0 : type_of(sn, a.cell_type, a.tp.obstacle_type)));
-                if (sn != si) adhesion += sm.J[ti * kMaxTypes + tn]; else ++mi;
-                if (sn != sj) adhesion -= sm.J[tj * kMaxTypes + tn]; else ++mj;
-            }
-            const int dAi = NB - 2 * mi, dAj = 2 * mj - NB;
-            int64_t dh = adhesion;
-            if (si > 0) {
-                dh += (int64_t)sm.lv[ti] * (2 * (Vi - sm.vt[ti]) + 1);
-                if (PERIM) dh += (int64_t)sm.lp[ti] * dAi * (2 * (Ai - sm.at[ti]) + dAi);
-            }
-            if (sj > 0) {
-                dh += (int64_t)sm.lv[tj] * (1 - 2 * ((int64_t)Vj - sm.vt[tj]));
-                if (PERIM) dh += (int64_t)sm.lp[tj] * dAj * (2 * (Aj - sm.at[tj]) + dAj);
-            }
-            int64_t dhq = 16 * dh;
-            if (a.chem || a.pers_dir) dhq += motility_q<3>(a, si, sj, ti, tj, ox, oy, oz, isite);
-            int decided = -1;  // 1 accept, 0 reject, -1 open
-            if (ACT) {
-                const int tp = si > 0 ? ti : tj;
-                const int64_t lam = sm.la[tp], mx = sm.ma[tp];
-                if (lam != 0 && mx != 0) {
-                    // the Act term's range decides the test without the geometric means when it can
-                    const int64_t lo = dhq + floor_div_pos(-lam * (si > 0 ? a.tp.gm_max[ti] : 0), mx * 4096);
-                    const int64_t hi = dhq + floor_div_pos(lam * (sj > 0 ? a.tp.gm_max[tj] : 0), mx * 4096);
-                    if (hi <= 0) decided = 1;
-                    else if (lo >= a.L || (lo > 0 && w.v[2] >= __ldg(a.thr + lo))) decided = 0;
-                    else {
-                        const int64_t gj = gm_words(a, sm, nbw, sj, sj > 0 ? sm.ma[tj] : 0);
-                        const int64_t gi = gm_q<3, 1>(a, sm, xs[ox], ys[oy], zs[oz], si, si > 0 ? sm.ma[ti] : 0);
-                        dhq += floor_div_pos(lam * (gj - gi), mx * 4096);
-                    }
-                }
-            }
-            const bool ok = decided >= 0 ? decided == 1 : (dhq <= 0 || (dhq < a.L && w.v[2] < __ldg(a.thr + dhq)));
-            if (ok) {
-                // a copy stamps the site with this MCS (a medium copy: age 128, no activity)
-                a.lat[j] = ACT && a.packed ? pack_word(si, si > 0 ? (a.t & 255u) : ((a.t - 128u) & 255u)) : si;
-                if (si > 0) { atomicAdd(a.Vn + si, 1); atomicAdd(a.An + si, dAi); }
-                if (sj > 0) { atomicAdd(a.Vn + sj, -1); atomicAdd(a.An + sj, dAj); }
-                a.pend_cur[i] = make_int4(si, sj, dAi, dAj);
-                accepted = true;
-            }
-        }
-    }
-    a.flag_cur[i] = accepted ? 1 : 0;
-    return accepted;
-}
-
 // Resident CTAs per SM (register budget): the round kernel is latency-bound.
 // Measured on GB300 in same-box A/B runs: without Act, four CTAs of 256
 // (64 registers) are fastest (256^3 cube cells: 1.05 ms per MCS against 1.31
@@ -437,16 +301,9 @@ __device__ __forceinline__ bool round_attempt3(const RoundArgs &a, const SmemTab
 #ifndef CPM_ROUND_MIN_BLOCKS_ACT
 #define CPM_ROUND_MIN_BLOCKS_ACT 8
 #endif
-// 3D (round_attempt3, CTAs of 128): the 26 neighbour words of a candidate are
-// held in registers, so the budget is 64 registers (eight CTAs per SM).
-#ifndef CPM_ROUND3_MIN_BLOCKS
-#define CPM_ROUND3_MIN_BLOCKS 8
-#endif
 
 template <int DIM, bool PERIM, bool ACT>
-__global__ void __launch_bounds__(DIM == 3 ? 128 : kThreads,
-                                  DIM == 3 ? CPM_ROUND3_MIN_BLOCKS
-                                           : (ACT ? CPM_ROUND_MIN_BLOCKS_ACT : CPM_ROUND_MIN_BLOCKS))
+__global__ void __launch_bounds__(kThreads, ACT ? CPM_ROUND_MIN_BLOCKS_ACT : CPM_ROUND_MIN_BLOCKS)
     round_kernel(const RoundArgs a)
 {
     __shared__ SmemTables sm;
@@ -467,10 +324,7 @@ __global__ void __launch_bounds__(DIM == 3 ? 128 : kThreads,
     const uint32_t i = ix + a.nax * (iy + a.nay * iz);
     bool accepted = false;
     if (valid) {
-        if (DIM == 3)
-            accepted = round_attempt3<PERIM, ACT>(a, sm, ix, iy, iz, i);
-        else
-            accepted = round_attempt<DIM, PERIM, ACT, ACT ? 1 : 0>(a, sm, ix, iy, iz, i);
+        accepted = round_attempt<DIM, PERIM, ACT, ACT ? 1 : 0>(a, sm, ix, iy, iz, i);
     }
     const unsigned m = __ballot_sync(0xffffffffu, accepted);
     if ((threadIdx.x & 31) == 0 && m != 0) atomicAdd(a.accepts, (unsigned long long)__popc(m));

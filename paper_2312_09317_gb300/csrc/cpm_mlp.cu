@@ -378,6 +378,7 @@ struct TcArgs {
     int epi, c_f32, vec_a, vec_b, vec_c;
     int mtiles, tiles;
     int *err;
+    int report_timeout;  // test hook: report the first accumulator wait as timed out once it has completed
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -514,7 +515,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) gemm_tc_kernel(const TcArgs p)
                              smem_u32(&mbar))
                          : "memory");
         }
-        const bool ok = tc_wait(&mbar, phase);
+        // (with report_timeout the wait still completes: the MMAs are done before the failure path runs)
+        const bool ok = tc_wait(&mbar, phase) && !p.report_timeout;
         phase ^= 1u;
         if (__syncthreads_or(!ok)) {
             aborted = true;
@@ -625,9 +627,10 @@ bool tc_eligible(int ta, int tb, const GemmArgs &a)
            a.K >= 1 && a.K <= 256;
 }
 
-int launch_gemm_tc(const GemmArgs &a, int batch, int *err, cudaStream_t st)
+int launch_gemm_tc(const GemmArgs &a, int batch, int *err, cudaStream_t st, int report_timeout)
 {
     TcArgs p{};
+    p.report_timeout = report_timeout;
     p.M = a.M;
     p.N = a.N;
     p.K = a.K;
@@ -686,15 +689,18 @@ int launch_gemm_tc(const GemmArgs &a, int batch, int *err, cudaStream_t st)
 }
 
 int launch_gemm(int ta, int tb, GemmArgs &a, int batch, cudaStream_t st, int *tc_err = nullptr,
-                bool allow_tc = true)
+                bool allow_tc = true, int *report_timeout = nullptr)
 {
     if (a.M == 0 || a.N == 0) return CPM_MLP_OK;
     // vector loads need 16-byte aligned rows: base, leading dimension and member stride
     a.vec_a = aligned16(a.A) && a.lda % 8 == 0 && a.sa % 8 == 0;
     a.vec_b = aligned16(a.B) && a.ldb % 8 == 0 && a.sb % 8 == 0;
     if (allow_tc && tc_eligible(ta, tb, a)) {
-        const int rc = launch_gemm_tc(a, batch, tc_err, st);
-        if (rc != kTcNotApplicable) return rc;
+        const int rc = launch_gemm_tc(a, batch, tc_err, st, report_timeout ? *report_timeout : 0);
+        if (rc != kTcNotApplicable) {
+            if (report_timeout) *report_timeout = 0;  // armed for one launch
+            return rc;
+        }
     }
     const dim3 grid((a.N + kBN - 1) / kBN, (a.M + kBM - 1) / kBM, batch);
     if (grid.y > 65535u || batch > 65535) return CPM_MLP_E_INVALID;
@@ -733,6 +739,7 @@ struct cpm_mlp {
     int have_transform = 0, have_rmse = 0;
     int64_t t = 0;
     uint64_t launches = 0;
+    int report_tc_timeout = 0;  // cpm_mlp_report_next_tc_timeout
     char err[256]{};
 };
 
@@ -810,7 +817,7 @@ int forward(cpm_mlp *h, int rows, bool keep_z)
             a.c_f32 = 1;
             a.epi = CPM_MLP_EPI_NONE;
         }
-        const int rc = launch_gemm(0, 1, a, h->sh.n_members, h->st, h->bad + 1);
+        const int rc = launch_gemm(0, 1, a, h->sh.n_members, h->st, h->bad + 1, true, &h->report_tc_timeout);
         if (rc) return fail(h, rc, "forward gemm launch failed");
         ++h->launches;
     }
@@ -1106,6 +1113,13 @@ int cpm_mlp_predict(cpm_mlp *h, const float *X, int64_t n_rows, float *mean_out,
 uint64_t cpm_mlp_kernel_launches(const cpm_mlp *h) { return h ? h->launches : 0; }
 
 const char *cpm_mlp_last_error(const cpm_mlp *h) { return h ? h->err : g_create_err; }
+
+int cpm_mlp_report_next_tc_timeout(cpm_mlp *h)
+{
+    if (!h) return CPM_MLP_E_INVALID;
+    h->report_tc_timeout = 1;
+    return CPM_MLP_OK;
+}
 
 int cpm_mlp_destroy(cpm_mlp *h)
 {

@@ -295,6 +295,27 @@ def test_bad_row_index_is_rejected(net):
     assert torch.isfinite(g).all()
 
 
+def test_tensor_core_wait_timeout_is_reported_and_the_handle_recovers(net):
+    """The failure path of the tensor-core GEMM's bounded accumulator wait:
+    armed through cpm_mlp_report_next_tc_timeout, the next forward layer
+    takes that path after its MMAs have completed (no GPU is stalled), the
+    call returns CPM_MLP_E_CUDA with the timeout message, and the same
+    handle then computes the same outputs as before the failure."""
+    from paper_2312_09317_gb300 import cpm
+    e, init = net
+    e.set_params(init)
+    X = torch.from_numpy(np.random.default_rng(11).uniform(0, 1, (700, 7)).astype(np.float32)).cuda()
+    ref = e.forward(X).clone()
+    assert e.lib.cpm_mlp_report_next_tc_timeout(e.h) == 0
+    with pytest.raises(cpm.CPMError) as exc:
+        e.forward(X)
+    assert exc.value.code == -3 and "tensor-core accumulator wait timed out" in str(exc.value)
+    again = e.forward(X)
+    torch.cuda.synchronize()
+    assert torch.equal(again, ref)
+    assert e.lib.cpm_mlp_report_next_tc_timeout(None) == -1
+
+
 def _observe_check(cpm, ws, n_mcs):
     b = cpm.Batch(ws)
     b.step(n_mcs)
