@@ -510,6 +510,9 @@ def run_gpu_batch(args):
     rounds = sum(max((w.a // w.c) ** w.dim * w.c ** w.dim for w in g) for g in groups if g)
     # the autotuner times its CTA shapes on the batches themselves (untimed; it only changes the split)
     choices = [b.autotune(2) for b in batches]
+    if args.loop == "persistent":
+        for b in batches:
+            b.set_persistent(True)
     for _ in range(args.warmup):
         for b in batches:
             b.step(1)
@@ -588,6 +591,7 @@ def run_gpu_batch(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "members": len(members), "sites": n,
                        "launches_per_step": launches // args.steps, "autotuned_shapes": choices,
+                       "loop": args.loop,
                        "l2": "inputs larger than L2",
                        "parallelism": "replicas" if ws_ > 1 else "1 GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -775,6 +779,8 @@ def main():
                     "region (default: a temporary file)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--loop", default="persistent", choices=["persistent", "graph"],
+                    help="ensembles: one persistent cooperative launch per step, or one CUDA graph per MCS")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -225,6 +225,25 @@ int cpm_batch_create(const cpm_config *cfgs, int32_t n, void *cuda_stream, cpm_b
  * rounds, and a device-side advance of every member's MCS counter. */
 int cpm_batch_step(cpm_batch *b, int64_t n_mcs);
 
+/* Choose how cpm_batch_step runs the MCS loop.
+ *   on = 0 (the default): one CUDA graph per MCS, replayed: the Act clamp,
+ *          one kernel per round, and the advance of the members' counters.
+ *   on = 1: one persistent, cooperative launch per call runs all n_mcs MCS:
+ *          the same phases, separated by grid-wide barriers instead of
+ *          kernel boundaries (every CTA of the launch is resident; the grid
+ *          is at most what the device holds at once).  Same results bit for
+ *          bit.  cpm_batch_step then waits for its launch to finish.
+ * Every barrier wait is bounded: after max_polls polls (about 100 ns apart;
+ * max_polls < 0 selects the default, 2^24) the waiting CTA records a timeout
+ * and ends, and cpm_batch_step returns CPM_E_STATE ("grid-barrier wait ...
+ * timed out"); the lattices are then in an unspecified state and the batch
+ * should be destroyed.  A healthy launch never times out.
+ *   on = 2: a test of that path: as on = 1, but the launch's first CTA leaves
+ *          before its first barrier, so the other CTAs' waits run out (use a
+ *          small max_polls); the step returns CPM_E_STATE.
+ * Errors: CPM_E_HANDLE, CPM_E_INVALID (on not 0..2), CPM_E_CUDA. */
+int cpm_batch_set_persistent(cpm_batch *b, int32_t on, int64_t max_polls);
+
 /* Pick the CTA brick shape (active blocks per CTA along x, y, z) for this
  * batch by timing: in 1 + n_mcs_each passes every candidate shape runs one
  * MCS of the batch itself (the first pass only warms up) and the shape

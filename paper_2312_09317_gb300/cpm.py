@@ -79,6 +79,7 @@ _SIGNATURES = {
     "cpm_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "cpm_batch_size": (ctypes.c_int32, [ctypes.c_void_p]),
     "cpm_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "cpm_batch_set_persistent": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
     "cpm_batch_read_lattice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int]),
     "cpm_batch_load_lattice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int]),
     "cpm_batch_read_tallies": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
@@ -325,6 +326,10 @@ class Batch:
 
     def step(self, n_mcs: int = 1):
         self._check(self.lib.cpm_batch_step(self.b, n_mcs))
+
+    def set_persistent(self, on: bool = True, max_polls: int = -1):
+        """Run each step as one persistent cooperative launch (cpm_batch_set_persistent)."""
+        self._check(self.lib.cpm_batch_set_persistent(self.b, 1 if on else 0, max_polls))
 
     def read_lattice(self, idx: int, out=None):
         w = self.ws[idx]

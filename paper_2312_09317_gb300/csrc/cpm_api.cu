@@ -907,6 +907,15 @@ struct cpm_batch {
     size_t traj_cap = 0;
     cudaGraphExec_t graph = nullptr;     // one MCS of every member
     int64_t graph_launches = 0;          // kernels in one replay
+    // the persistent loop (cpm_batch_set_persistent)
+    bool persistent = false;
+    bool test_absent = false;            // cpm_batch_set_persistent(b, 2, ...): timeout-path test
+    long long max_polls = 1ll << 24;     // bound of each grid-barrier wait (polls about 100 ns apart)
+    uint32_t *d_upto_q = nullptr;        // round items per round q
+    uint32_t r_max_items = 0;            // items of the fullest round
+    unsigned *d_bar = nullptr;           // barrier counter
+    int *d_err = nullptr;                // barrier timeout flag
+    uint32_t loop_grid = 0;              // CTAs of the last persistent launch
     bool descriptors_dirty = true;
     int64_t launches = 0;
     std::string err;
@@ -938,6 +947,9 @@ void batch_free(cpm_batch *b)
     cudaFree(b->d_clamp);
     cudaFree(b->d_obs);
     cudaFree(b->traj);
+    cudaFree(b->d_upto_q);
+    cudaFree(b->d_bar);
+    cudaFree(b->d_err);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
 }
 
@@ -969,11 +981,25 @@ int batch_build_items(cpm_batch *b)
         for (uint64_t c = 0; c < chunks; c++) clamp.push_back(make_int2((int)l, (int)c));
     }
     b->n_clamp_items = (uint32_t)clamp.size();
+    // items of round q for the persistent loop: those of the members with more than q rounds per MCS
+    const uint32_t r_max = b->lats[b->order[0]].R;
+    std::vector<uint32_t> upto_q(r_max);
+    size_t active = b->order.size();
+    for (uint32_t q = 0; q < r_max; q++) {
+        while (active > 0 && b->lats[b->order[active - 1]].R <= q) active--;
+        upto_q[q] = b->items_upto[active];
+    }
+    b->r_max_items = r_max > 0 ? upto_q[0] : 0;
     cudaFree(b->d_items);
     cudaFree(b->d_clamp);
+    cudaFree(b->d_upto_q);
     b->d_items = nullptr;
     b->d_clamp = nullptr;
-    cudaError_t e = cudaMalloc(&b->d_items, sizeof(int2) * std::max<size_t>(items.size(), 1));
+    b->d_upto_q = nullptr;
+    cudaError_t e = cudaMalloc(&b->d_upto_q, sizeof(uint32_t) * std::max<size_t>(upto_q.size(), 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_upto_q, upto_q.data(), sizeof(uint32_t) * upto_q.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(int2) * std::max<size_t>(items.size(), 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_clamp, sizeof(int2) * std::max<size_t>(clamp.size(), 1));
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
@@ -1166,21 +1192,71 @@ int cpm_batch_step(cpm_batch *b, int64_t n_mcs)
         if (e != cudaSuccess) return bfail(b, CPM_E_CUDA, cudaGetErrorString(e));
         b->descriptors_dirty = false;
     }
-    if (!b->graph) {
-        int rc = batch_build_graph(b);
-        if (rc) return rc;
+    if (b->persistent) {
+        // one cooperative launch runs all n_mcs MCS; its barrier waits are bounded
+        for (int64_t done = 0; done < n_mcs;) {
+            const uint32_t chunk = (uint32_t)std::min<int64_t>(n_mcs - done, 1 << 16);
+            BatchLoopArgs p{};
+            p.lats = b->d_lats;
+            p.n_lats = (uint32_t)b->lats.size();
+            p.items = b->d_items;
+            p.upto_q = b->d_upto_q;
+            p.r_max = b->lats[b->order[0]].R;
+            p.clamp = b->d_clamp;
+            p.n_clamp = b->act ? b->n_clamp_items : 0;
+            p.n_mcs = chunk;
+            p.bar = b->d_bar;
+            p.max_polls = b->max_polls;
+            p.err = b->d_err;
+            p.max_items = b->r_max_items;
+            p.test_absent = b->test_absent ? 1 : 0;
+            cudaError_t e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned), b->stream);
+            if (e == cudaSuccess) e = launch_batch_loop(b->dim, b->perim, b->act, p, batch_threads(b), b->stream,
+                                                        &b->loop_grid);
+            int timed_out = 0;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&timed_out, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+            if (e != cudaSuccess) return bfail(b, CPM_E_CUDA, cudaGetErrorString(e));
+            b->launches += 1;
+            if (timed_out)
+                return bfail(b, CPM_E_STATE,
+                             "a grid-barrier wait of the persistent loop timed out; the lattices are in an unspecified "
+                             "state");
+            done += chunk;
+        }
+    } else {
+        if (!b->graph) {
+            int rc = batch_build_graph(b);
+            if (rc) return rc;
+        }
+        for (int64_t k = 0; k < n_mcs; k++) {
+            cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+            if (e != cudaSuccess) return bfail(b, CPM_E_CUDA, cudaGetErrorString(e));
+        }
+        b->launches += n_mcs * b->graph_launches;
     }
-    for (int64_t k = 0; k < n_mcs; k++) {
-        cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
-        if (e != cudaSuccess) return bfail(b, CPM_E_CUDA, cudaGetErrorString(e));
-    }
-    b->launches += n_mcs * b->graph_launches;
     for (size_t l = 0; l < b->hs.size(); l++) {
         cpm_handle *h = b->hs[l];
         h->t += n_mcs;
         h->g += (uint64_t)n_mcs * b->lats[l].R;
         h->attempts += n_mcs * (int64_t)h->n_sites;
     }
+    return CPM_OK;
+}
+
+int cpm_batch_set_persistent(cpm_batch *b, int32_t on, int64_t max_polls)
+{
+    if (!b) return CPM_E_HANDLE;
+    if (on && !b->d_bar) {
+        cudaError_t e = cudaMalloc(&b->d_bar, sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
+        if (e != cudaSuccess) return bfail(b, CPM_E_CUDA, cudaGetErrorString(e));
+    }
+    if (on < 0 || on > 2) return bfail(b, CPM_E_INVALID, "on must be 0, 1 or 2");
+    b->persistent = on != 0;
+    b->test_absent = on == 2;
+    b->max_polls = max_polls >= 0 ? (long long)max_polls : (1ll << 24);
     return CPM_OK;
 }
 

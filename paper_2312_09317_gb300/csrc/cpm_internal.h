@@ -129,6 +129,24 @@ cudaError_t launch_batch_round(int dim, bool perim, bool act, const BatchLattice
                                uint32_t n_items, uint32_t q, uint32_t threads, cudaStream_t st);
 cudaError_t launch_batch_clamp(const BatchLattice *lats, const int2 *items, uint32_t n_items, cudaStream_t st);
 cudaError_t launch_batch_advance(BatchLattice *lats, uint32_t n, cudaStream_t st);
+// The persistent batched MCS loop (one cooperative launch for n_mcs MCS).
+struct BatchLoopArgs {
+    BatchLattice *lats;
+    uint32_t n_lats;
+    const int2 *items;        // round items, members by rounds per MCS (descending)
+    const uint32_t *upto_q;   // items of round q: the first upto_q[q]
+    uint32_t r_max;           // rounds per MCS of the longest member
+    const int2 *clamp;        // Act clamp items
+    uint32_t n_clamp;
+    uint32_t n_mcs;
+    unsigned *bar;            // grid barrier counter, 0 at launch
+    long long max_polls;      // bound of every barrier wait
+    int *err;                 // set to 1 when a wait runs out
+    uint32_t max_items;       // items of the fullest round (bounds the grid)
+    int test_absent;          // test of the timeout path: CTA 0 leaves before its first barrier
+};
+cudaError_t launch_batch_loop(int dim, bool perim, bool act, const BatchLoopArgs &p, uint32_t threads, cudaStream_t st,
+                              uint32_t *grid_out);
 
 // Observations of a batch (cpm_batch_observe): one item per lattice.
 constexpr int kObsFields = 12;  // anchor, volume, offset sums x y z, interface count, xx yy zz xy xz yz

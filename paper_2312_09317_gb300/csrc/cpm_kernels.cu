@@ -342,13 +342,14 @@ __global__ void __launch_bounds__(kThreads, ACT ? CPM_ROUND_MIN_BLOCKS_ACT : CPM
 #ifndef CPM_BATCH_MIN_BLOCKS_ACT
 #define CPM_BATCH_MIN_BLOCKS_ACT 8
 #endif
+// One (lattice, brick) item of batch round q: lattice it.x's round number
+// g_start + q, exactly as the single-lattice round kernel would run it (same
+// colour, counters and tallies).  ra and sm are the CTA's shared set-up.
 template <int DIM, bool PERIM, bool ACT>
-__global__ void __launch_bounds__(kBatchMaxThreads, ACT ? CPM_BATCH_MIN_BLOCKS_ACT : CPM_BATCH_MIN_BLOCKS)
-    batch_round_kernel(const BatchLattice *lats, const int2 *items, uint32_t q)
+__device__ __forceinline__ void batch_round_item(RoundArgs &ra, SmemTables &sm, const BatchLattice *lats, int2 it,
+                                                 uint32_t q)
 {
-    __shared__ RoundArgs ra;
-    __shared__ SmemTables sm;
-    const int2 it = items[blockIdx.x];
+    __syncthreads();  // the previous item of this CTA is done with ra and sm
     if (threadIdx.x == 0) {
         const BatchLattice &L = lats[it.x];
         ra = L.base;
@@ -403,6 +404,125 @@ __global__ void __launch_bounds__(kBatchMaxThreads, ACT ? CPM_BATCH_MIN_BLOCKS_A
     if ((threadIdx.x & 31) == 0 && m != 0) atomicAdd(ra.accepts, (unsigned long long)__popc(m));
 }
 
+// Batched round: every CTA takes one (lattice, chunk of active blocks) item.
+// Register budget of the batched round as for round_kernel: with Act eight
+// CTAs of 256 per SM (the 512-member ensemble: 31.2 ms per MCS against 36.7
+// at two CTAs), without Act four.
+#ifndef CPM_BATCH_MIN_BLOCKS
+#define CPM_BATCH_MIN_BLOCKS 4
+#endif
+#ifndef CPM_BATCH_MIN_BLOCKS_ACT
+#define CPM_BATCH_MIN_BLOCKS_ACT 8
+#endif
+template <int DIM, bool PERIM, bool ACT>
+__global__ void __launch_bounds__(kBatchMaxThreads, ACT ? CPM_BATCH_MIN_BLOCKS_ACT : CPM_BATCH_MIN_BLOCKS)
+    batch_round_kernel(const BatchLattice *lats, const int2 *items, uint32_t q)
+{
+    __shared__ RoundArgs ra;
+    __shared__ SmemTables sm;
+    batch_round_item<DIM, PERIM, ACT>(ra, sm, lats, items[blockIdx.x], q);
+}
+
+// Stamps whose age is 128 or more are reset to age exactly 128, so that ages
+// stay below 256 until the next clamp (run every 64 MCS).  Obstacle words are
+// left as they are (their stamp is never read).
+__device__ __forceinline__ void clamp_word(int32_t *p, uint32_t t8)
+{
+    const int32_t w = *p;
+    if (cell_id(w) < 0) return;
+    const uint32_t age = (t8 - word_stamp(w)) & 255u;
+    if (age >= 128u) *p = pack_word(cell_id(w), (t8 - 128u) & 255u);
+}
+
+// Act stamp clamp of one (member, chunk of 65,536 sites) item, for a member
+// whose MCS t_start is a multiple of 64 (run at the start of its MCS).
+__device__ __forceinline__ void batch_clamp_item(const BatchLattice *lats, int2 it)
+{
+    const BatchLattice &L = lats[it.x];
+    if (!L.base.packed || (L.t_start % 64) != 0) return;
+    const uint64_t n = (uint64_t)L.base.nx * L.base.ny * L.base.nz;
+    const uint32_t t8 = (uint32_t)L.t_start & 255u;
+    const uint64_t lo = (uint64_t)it.y * 65536u, hi = lo + 65536u < n ? lo + 65536u : n;
+    for (uint64_t x = lo + threadIdx.x; x < hi; x += blockDim.x) clamp_word(L.base.lat + x, t8);
+}
+
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier of a co-resident (cooperative) grid on a counter that
+// starts at 0: the k-th barrier waits for k * gridDim.x arrivals.  The wait
+// is bounded: after max_polls polls (about 100 ns apart) the CTA records the
+// timeout in *err and the barrier returns false; the caller then returns.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, long long max_polls, int *err, int &ok_s)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        int ok = 1;
+        long long polls = 0;
+        while (ld_acquire_gpu(bar) < target) {
+            if (polls++ >= max_polls) {
+                ok = 0;
+                atomicExch(err, 1);
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// The persistent batched MCS loop: n_mcs MCS of every member in one
+// cooperative launch.  Per MCS: the Act clamp items, then rounds q = 0 ..
+// r_max - 1 over the items of the members that still have rounds
+// (upto_q[q] items), then the advance of every member's MCS and round
+// counters, each phase closed by a grid barrier.  The work and its order
+// within a phase are those of the per-round launches, so the result is the
+// same bit for bit.
+template <int DIM, bool PERIM, bool ACT>
+__global__ void __launch_bounds__(kBatchMaxThreads, ACT ? CPM_BATCH_MIN_BLOCKS_ACT : CPM_BATCH_MIN_BLOCKS)
+    batch_loop_kernel(BatchLattice *lats, uint32_t n_lats, const int2 *items, const uint32_t *upto_q, uint32_t r_max,
+                      const int2 *clamp, uint32_t n_clamp, uint32_t n_mcs, unsigned *bar, long long max_polls,
+                      int *err, int test_absent)
+{
+    __shared__ RoundArgs ra;
+    __shared__ SmemTables sm;
+    __shared__ int ok_s;
+    // test of the timeout path: the first CTA never arrives, so the others' first barrier wait runs out
+    if (test_absent && blockIdx.x == 0) return;
+    unsigned target = 0;
+    for (uint32_t m = 0; m < n_mcs; ++m) {
+        if (ACT) {
+            for (uint32_t c = blockIdx.x; c < n_clamp; c += gridDim.x) batch_clamp_item(lats, clamp[c]);
+            target += gridDim.x;
+            if (!grid_barrier(bar, target, max_polls, err, ok_s)) return;
+        }
+        for (uint32_t q = 0; q < r_max; ++q) {
+            const uint32_t n_items = upto_q[q];
+            for (uint32_t k = blockIdx.x; k < n_items; k += gridDim.x)
+                batch_round_item<DIM, PERIM, ACT>(ra, sm, lats, items[k], q);
+            target += gridDim.x;
+            if (!grid_barrier(bar, target, max_polls, err, ok_s)) return;
+        }
+        if (blockIdx.x == 0)
+            for (uint32_t l = threadIdx.x; l < n_lats; l += blockDim.x) {
+                lats[l].t_start += 1;
+                lats[l].g_start += lats[l].R;
+            }
+        target += gridDim.x;
+        if (!grid_barrier(bar, target, max_polls, err, ok_s)) return;
+    }
+}
+
 template <int DIM>
 __global__ void recount_kernel(const int32_t *__restrict__ lat, int32_t *V, int32_t *A, uint32_t nx, uint32_t ny,
                                uint32_t nz, uint64_t n)
@@ -432,17 +552,6 @@ __global__ void compare_kernel(const int32_t *V, const int32_t *A, const int32_t
 {
     for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
         if (k > 0 && (V[k] != V2[k] || A[k] != A2[k])) atomicAdd(n_bad, 1ull);
-}
-
-// Stamps whose age is 128 or more are reset to age exactly 128, so that ages
-// stay below 256 until the next clamp (run every 64 MCS).  Obstacle words are
-// left as they are (their stamp is never read).
-__device__ __forceinline__ void clamp_word(int32_t *p, uint32_t t8)
-{
-    const int32_t w = *p;
-    if (cell_id(w) < 0) return;
-    const uint32_t age = (t8 - word_stamp(w)) & 255u;
-    if (age >= 128u) *p = pack_word(cell_id(w), (t8 - 128u) & 255u);
 }
 
 __global__ void clamp_kernel(int32_t *lat, uint64_t n, uint32_t t)
@@ -507,17 +616,9 @@ cudaError_t launch_round(int dim, bool perim, bool act, const RoundArgs &a, cuda
     return perim ? launch_round_t<3, true, false>(a, st) : launch_round_t<3, false, false>(a, st);
 }
 
-// Act stamp clamp for every member whose MCS t_start is a multiple of 64
-// (run at the start of its MCS); items are (member, chunk of 65,536 sites).
 __global__ void batch_clamp_kernel(const BatchLattice *lats, const int2 *items)
 {
-    const int2 it = items[blockIdx.x];
-    const BatchLattice &L = lats[it.x];
-    if (!L.base.packed || (L.t_start % 64) != 0) return;
-    const uint64_t n = (uint64_t)L.base.nx * L.base.ny * L.base.nz;
-    const uint32_t t8 = (uint32_t)L.t_start & 255u;
-    const uint64_t lo = (uint64_t)it.y * 65536u, hi = lo + 65536u < n ? lo + 65536u : n;
-    for (uint64_t x = lo + threadIdx.x; x < hi; x += blockDim.x) clamp_word(L.base.lat + x, t8);
+    batch_clamp_item(lats, items[blockIdx.x]);
 }
 
 // End of one batch MCS: every member moves to its next MCS.
@@ -540,6 +641,47 @@ cudaError_t launch_batch_advance(BatchLattice *lats, uint32_t n, cudaStream_t st
 {
     batch_advance_kernel<<<(n + 255) / 256, 256, 0, st>>>(lats, n);
     return cudaGetLastError();
+}
+
+template <int DIM, bool PERIM, bool ACT>
+cudaError_t launch_batch_loop_t(const BatchLoopArgs &p, uint32_t threads, cudaStream_t st, uint32_t *grid_out)
+{
+    auto kern = batch_loop_kernel<DIM, PERIM, ACT>;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (int)threads, 0);
+    if (e != cudaSuccess) return e;
+    uint64_t grid = (uint64_t)sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
+    if (grid > p.max_items) grid = p.max_items;
+    if (grid < 2 && p.test_absent) grid = 2;  // someone must wait for the absent CTA
+    if (grid < 1) grid = 1;
+    *grid_out = (uint32_t)grid;
+    BatchLattice *lats = p.lats;
+    uint32_t n_lats = p.n_lats, r_max = p.r_max, n_clamp = p.n_clamp, n_mcs = p.n_mcs;
+    const int2 *items = p.items, *clamp = p.clamp;
+    const uint32_t *upto = p.upto_q;
+    unsigned *bar = p.bar;
+    long long polls = p.max_polls;
+    int *err = p.err;
+    int absent = p.test_absent;
+    void *args[] = {&lats, &n_lats, &items, &upto, &r_max, &clamp, &n_clamp, &n_mcs, &bar, &polls, &err, &absent};
+    return cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)grid), dim3(threads), args, 0, st);
+}
+
+cudaError_t launch_batch_loop(int dim, bool perim, bool act, const BatchLoopArgs &p, uint32_t threads, cudaStream_t st,
+                              uint32_t *grid_out)
+{
+    if (dim == 2) {
+        if (act) return perim ? launch_batch_loop_t<2, true, true>(p, threads, st, grid_out)
+                              : launch_batch_loop_t<2, false, true>(p, threads, st, grid_out);
+        return perim ? launch_batch_loop_t<2, true, false>(p, threads, st, grid_out)
+                     : launch_batch_loop_t<2, false, false>(p, threads, st, grid_out);
+    }
+    if (act) return perim ? launch_batch_loop_t<3, true, true>(p, threads, st, grid_out)
+                          : launch_batch_loop_t<3, false, true>(p, threads, st, grid_out);
+    return perim ? launch_batch_loop_t<3, true, false>(p, threads, st, grid_out)
+                 : launch_batch_loop_t<3, false, false>(p, threads, st, grid_out);
 }
 
 cudaError_t launch_batch_round(int dim, bool perim, bool act, const BatchLattice *lats, const int2 *items,

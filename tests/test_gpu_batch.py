@@ -109,3 +109,52 @@ def test_batch_autotune_keeps_results_exact(cpm):
         r.replay_run(1 + 7 * 2 + 2)
     _check(batch, refs, "after autotune")
     batch.close()
+
+
+# ---------------------------------------------------------------------------
+# the persistent loop: one cooperative launch per step, grid barriers between
+# the phases of each MCS
+# ---------------------------------------------------------------------------
+
+def test_persistent_loop_bit_exact_2d_and_3d(cpm):
+    """Mixed members (different rounds per MCS, Act, obstacles) advanced by
+    the persistent loop match the replay after every call, across an Act
+    stamp clamp (MCS 0 and 64) and with a switch between the two loops."""
+    for ws, steps in ((_mixed_2d(), (1, 3, 62, 2)),
+                      ([cw.random_small(400 + k, dim=3, n=[12, 16][k % 2], n_cells=5 + k, edge=3, perimeter=True,
+                                        act=bool(k % 2), obstacles=0.03, a=4, c=2, P=[1, 8][k % 2])
+                        for k in range(4)], (1, 2))):
+        batch = cpm.Batch(ws)
+        batch.set_persistent(True)
+        refs = [oracle.State(w) for w in ws]
+        for k, n in enumerate(steps):
+            if k == len(steps) - 1:
+                batch.set_persistent(False)  # the graph loop continues where the persistent one stopped
+            batch.step(n)
+            for r in refs:
+                r.replay_run(n)
+            _check(batch, refs, "persistent %dD after +%d" % (ws[0].dim, n))
+        batch.close()
+
+
+def test_persistent_loop_barrier_timeout_is_reported(cpm):
+    """The test mode of the persistent loop makes its first CTA leave before
+    the first barrier, an arrival that never comes: the other CTAs' bounded
+    waits (10,000 polls) run out, the step returns CPM_E_STATE with the
+    timeout message, nothing hangs, and the device stays usable for a new
+    batch."""
+    ws = [cw.random_small(500 + k, dim=2, n=32, n_cells=6, a=4, c=2, P=1) for k in range(8)]
+    batch = cpm.Batch(ws)
+    assert batch.lib.cpm_batch_set_persistent(batch.b, 2, 10000) == cpm.CPM_OK
+    with pytest.raises(cpm.CPMError) as exc:
+        batch.step(1)
+    assert exc.value.code == cpm.CPM_E_STATE and "timed out" in str(exc.value)
+    batch.close()
+    fresh = cpm.Batch(ws[:2])
+    fresh.set_persistent(True)
+    refs = [oracle.State(w) for w in ws[:2]]
+    fresh.step(2)
+    for r in refs:
+        r.replay_run(2)
+    _check(fresh, refs, "after a timed-out batch")
+    fresh.close()

@@ -1,24 +1,27 @@
-"""Statistical parity of the GPU sweep with the serial CPM (oracle (a)).
+"""Statistical parity of the GPU sweep with the serial CPM (oracle (a)) on the
+2D workload (200x200, Moore-8, 100 cells, V_t = 100).
 
-The GPU path equals the parallel-scheme replay bit for bit; this test measures
-what the parallel scheme itself changes relative to the serial Markov chain,
-as the paper does for its own scheme (Results, Fig. 3-5): 32 seeds of the 2D
-workload (200x200, Moore-8, 100 cells, V_t = 100), 200 MCS of growth, then
-statistics over 100 MCS sampled every 10 MCS: cell volume mean and variance,
-perimeter (interface count) mean, acceptance rate, and the mean squared
-displacement of cell centroids over 10 and 50 MCS.
+The GPU path equals the parallel-scheme replay bit for bit; this test
+measures what the parallel scheme itself changes relative to the serial
+Markov chain, as the paper does for its own scheme (Results, Fig. 3-5):
+64 seeds, 200 MCS of growth, then 40 snapshots 10 MCS apart; cell volume
+mean and variance, interface-count mean, acceptance rate, and the mean
+squared displacement of cell centroids over 10 and 50 MCS
+(tests/tissue_stats.py reduces both sides).
 
-Tolerances (relative, per statistic, over the 32-seed means):
-* large areas with frequent switching, as the paper recommends (Results,
-  "Aligning the lattice update statistics"): areas of 20x20 sites, 2x2
-  checkerboard, 100 colour cycles per MCS (one round per visit).  The scheme
-  matches the serial chain within 2% on volume mean, perimeter mean and
-  acceptance, within 5% on volume variance and MSD (their 32-seed standard
-  errors are 1-1.5%);
-* the paper's sorting setting (4x4 areas, 2x2 checkerboard, one cycle): the
-  volume mean still matches within 2%, while fluctuation statistics differ
-  (several concurrent attempts on one cell inside a round); the test records
-  them and bounds them loosely.
+* Large areas with frequent switching, as the paper recommends (Results,
+  "Aligning the lattice update statistics"): areas of 40x40 sites, 2x2
+  checkerboard, one round per colour visit (P = 400).  Every statistic's
+  64-seed mean matches the serial chain's within 2%; the standard errors of
+  those means are at most 0.6% (variance and MSD over 50 MCS), so the bar
+  is about three standard errors of the difference wide.  (Areas of 20x20
+  come out at +1.4% volume variance and +1.8% MSD over 50 MCS, too close to
+  the bar; 10x10 at +13% variance.)
+* The paper's sorting setting (4x4 areas, 2x2 checkerboard, one cycle): the
+  mean volume still matches within 2%, and the deviations of the fluctuation
+  statistics that several concurrent attempts on one cell inside a round
+  cause are checked to be present (variance and acceptance far above the
+  serial chain's), as recorded in the design notes.
 """
 import multiprocessing as mp
 from concurrent.futures import ProcessPoolExecutor
@@ -27,84 +30,64 @@ import numpy as np
 import pytest
 
 import cpm_workloads as cw
+from tests import tissue_stats as ts
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-SEEDS = list(range(1, 33))
-BURN, SAMPLES, EVERY = 200, 10, 10
+SEEDS = list(range(1, 65))
+BURN, SNAPS, EVERY = 200, 40, 10
+TOL = 0.02
 
 
-def centroids(lat, n_cells):
-    """Periodic centroids (circular mean per axis) of every cell."""
-    lat2 = lat.reshape(lat.shape[-2], lat.shape[-1])
-    ids = lat2.ravel()
-    m = ids > 0
-    ys, xs = np.unravel_index(np.nonzero(m)[0], lat2.shape)
-    out = np.zeros((n_cells + 1, 2))
-    for d, (coord, L) in enumerate(((ys, lat2.shape[0]), (xs, lat2.shape[1]))):
-        ang = coord * 2 * np.pi / L
-        cs = np.bincount(ids[m], weights=np.cos(ang), minlength=n_cells + 1)
-        sn = np.bincount(ids[m], weights=np.sin(ang), minlength=n_cells + 1)
-        out[:, d] = (np.arctan2(sn, cs) % (2 * np.pi)) * L / (2 * np.pi)
-    return out
-
-
-def summarise(snapshots, tallies, accepts, n_sites, n_cells, shape):
-    L = np.array(shape, dtype=float)
-    traj = [np.zeros((n_cells + 1, 2))]
-    prev = centroids(snapshots[0], n_cells)
-    for s in snapshots[1:]:
-        c = centroids(s, n_cells)
-        d = c - prev
-        d -= np.round(d / L) * L
-        traj.append(traj[-1] + d)
-        prev = c
-    traj = np.array(traj)[:, 1:, :]
-    V = np.array([t[0][1:] for t in tallies], dtype=float)
-    A = np.array([t[1][1:] for t in tallies], dtype=float)
-    msd10 = ((traj[1:] - traj[:-1]) ** 2).sum(-1).mean()
-    msd50 = ((traj[5:] - traj[:-5]) ** 2).sum(-1).mean()
-    return dict(vmean=V.mean(), vvar=V.var(), amean=A.mean(), acc=accepts / (SAMPLES * EVERY * n_sites),
-                msd10=msd10, msd50=msd50)
-
-
-def run_serial(args):
-    seed, a = args
+def run_serial(seed):
+    import torch as th
+    th.set_num_threads(1)
     import oracle
-    w = cw.point_cells_2d(seed=seed, a=a, c=2, P=1)  # the schedule does not enter the serial chain
+    w = cw.point_cells_2d(seed=seed)  # the schedule does not enter the serial chain
     st = oracle.State(w)
     st.serial_run(BURN)
-    snaps, tall, acc = [st.lattice.copy()], [], 0
-    for _ in range(SAMPLES):
+    shape = (1, w.ny, w.nx)
+    rec = ts.Recorder(shape, w.n_cells)
+    rec.snapshot(th.from_numpy(st.lattice.reshape(shape)))
+    acc = 0
+    for _ in range(SNAPS):
         acc += st.serial_run(EVERY)
-        snaps.append(st.lattice.copy())
-        tall.append((st.V.copy(), st.A.copy()))
-    return summarise(snaps, tall, acc, w.n_sites, w.n_cells, (w.ny, w.nx))
+        rec.snapshot(th.from_numpy(st.lattice.reshape(shape)), st.V, st.A)
+    return rec.summary(acc, w.n_sites)
 
 
-def run_gpu(cpm, seed, a, P):
-    w = cw.point_cells_2d(seed=seed, a=a, c=2, P=P)
-    sim = cpm.Sim(w)
-    sim.step(BURN)
-    snaps, tall = [sim.read_lattice()], []
-    acc0 = sim.stats()["accepts"]
-    for _ in range(SAMPLES):
-        sim.step(EVERY)
-        snaps.append(sim.read_lattice())
-        tall.append(sim.read_tallies())
-    acc = sim.stats()["accepts"] - acc0
-    sim.close()
-    return summarise(snaps, tall, acc, w.n_sites, w.n_cells, (w.ny, w.nx))
+def run_gpu(cpm, a, P):
+    """All seeds as one batch (each member is exactly its single-lattice run)."""
+    ws = [cw.point_cells_2d(seed=s, a=a, c=2, P=P) for s in SEEDS]
+    b = cpm.Batch(ws)
+    b.step(BURN)
+    shape = (1, ws[0].ny, ws[0].nx)
+    recs = [ts.Recorder(shape, w.n_cells) for w in ws]
+    lat = torch.empty(shape, dtype=torch.int32, device="cuda")
+    for k, r in enumerate(recs):
+        b.read_lattice(k, lat)
+        r.snapshot(lat)
+    acc0 = [b.stats(k)["accepts"] for k in range(len(ws))]
+    for _ in range(SNAPS):
+        b.step(EVERY)
+        for k, r in enumerate(recs):
+            b.read_lattice(k, lat)
+            V, A = b.read_tallies(k)
+            r.snapshot(lat, V, A)
+    out = [r.summary(b.stats(k)["accepts"] - acc0[k], ws[k].n_sites) for k, r in enumerate(recs)]
+    b.close()
+    return {k: np.array([o[k] for o in out]) for k in ts.STATS}
 
 
 @pytest.fixture(scope="module")
 def serial_stats():
+    assert ts.EVERY == EVERY
     # the pool is started with spawn, independent of the GPU context
     ctx = mp.get_context("spawn")
     with ProcessPoolExecutor(max_workers=min(16, mp.cpu_count()), mp_context=ctx) as ex:
-        res = list(ex.map(run_serial, [(s, 4) for s in SEEDS]))
-    return {k: np.array([r[k] for r in res]) for k in res[0]}
+        res = list(ex.map(run_serial, SEEDS))
+    return {k: np.array([r[k] for r in res]) for k in ts.STATS}
 
 
 @pytest.fixture(scope="module")
@@ -118,36 +101,32 @@ def cpm():
     return m
 
 
-def _gpu_stats(cpm, a, P):
-    res = [run_gpu(cpm, s, a, P) for s in SEEDS]
-    return {k: np.array([r[k] for r in res]) for k in res[0]}
-
-
 def _rel(g, s):
-    return abs(g.mean() - s.mean()) / abs(s.mean())
+    return (g.mean() - s.mean()) / abs(s.mean())
+
+
+def _report(g, s):
+    return {k: dict(gpu=round(float(g[k].mean()), 6), serial=round(float(s[k].mean()), 6),
+                    rel=round(float(_rel(g[k], s[k])), 5),
+                    se_rel=round(float(np.sqrt(g[k].var(ddof=1) / len(g[k]) + s[k].var(ddof=1) / len(s[k]))
+                                       / abs(s[k].mean())), 5)) for k in ts.STATS}
 
 
 def test_statistics_match_serial_with_large_areas_frequent_switching(cpm, serial_stats):
-    g = _gpu_stats(cpm, 20, 100)
-    s = serial_stats
-    report = {k: (round(float(g[k].mean()), 5), round(float(s[k].mean()), 5), round(_rel(g[k], s[k]), 4))
-              for k in s}
-    print("a=20, P=100 (gpu, serial, rel):", report)
-    for k in ("vmean", "amean", "acc"):
-        assert _rel(g[k], s[k]) <= 0.02, (k, report)
-    for k in ("vvar", "msd10", "msd50"):
-        assert _rel(g[k], s[k]) <= 0.05, (k, report)
+    g = run_gpu(cpm, 40, 400)
+    rep = _report(g, serial_stats)
+    print("a=40, P=400:", rep)
+    for k in ts.STATS:
+        assert abs(rep[k]["rel"]) <= TOL, (k, rep)
 
 
 def test_statistics_with_the_papers_4x4_areas(cpm, serial_stats):
-    g = _gpu_stats(cpm, 4, 1)
+    g = run_gpu(cpm, 4, 1)
     s = serial_stats
-    report = {k: (round(float(g[k].mean()), 5), round(float(s[k].mean()), 5), round(_rel(g[k], s[k]), 4))
-              for k in s}
-    print("a=4 (gpu, serial, rel):", report)
-    assert _rel(g["vmean"], s["vmean"]) <= 0.02, report
-    # documented deviations of the 4x4/2x2 setting (in-round concurrency on one cell)
-    assert g["amean"].mean() > s["amean"].mean()
-    assert _rel(g["amean"], s["amean"]) <= 0.25, report
-    assert _rel(g["acc"], s["acc"]) <= 1.5, report
-    assert _rel(g["msd50"], s["msd50"]) <= 2.0, report
+    rep = _report(g, s)
+    print("a=4, P=1:", rep)
+    assert abs(rep["vmean"]["rel"]) <= TOL, rep
+    # the deviations of the 4x4 / 2x2 setting (in-round concurrency on one cell)
+    assert rep["vvar"]["rel"] > 0.5, rep
+    assert rep["acc"]["rel"] > 0.2, rep
+    assert rep["amean"]["rel"] > 0.02, rep
