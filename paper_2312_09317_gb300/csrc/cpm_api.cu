@@ -252,6 +252,7 @@ int run_subpass(cpm_handle *h)
     memset(&a, 0, sizeof a);
     a.lat = h->lat;
     a.packed = h->act ? 1u : 0u;
+    a.stream_loads = h->act && h->cfg.a >= 8 ? 1u : 0u;
     a.cell_type = h->cell_type;
     a.thr = h->thr;
     a.ln_tab = h->ln_tab;
@@ -1121,6 +1122,7 @@ int cpm_batch_create(const cpm_config *cfgs, int32_t n, void *cuda_stream, cpm_b
         RoundArgs &a = L.base;
         a.lat = h->lat;
         a.packed = h->act ? 1u : 0u;
+        a.stream_loads = h->act && h->cfg.a >= 8 ? 1u : 0u;
         a.cell_type = h->cell_type;
         a.thr = h->thr;
         a.ln_tab = h->ln_tab;
