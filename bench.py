@@ -465,6 +465,19 @@ def run_gpu(args):
                              "config": sl["config"], **sl["sweep"], "roofline": sl["roofline"]}
         except Exception as exc:  # reported, not fatal: the sweep is the second half of the line
             line["sweep"] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+    if rank == 0 and ws == 1 and args.workload == DEFAULT_WORKLOAD and not args.no_ensemble:
+        # the batched ensemble of the parameter sweep (512 lattices of uneven sizes), measured as
+        # `--workload cpm_ensemble_512` does, without its CPU baseline
+        try:
+            import argparse as _ap
+            ea = _ap.Namespace(**vars(args))
+            ea.workload, ea.steps, ea.warmup, ea.no_cpu_baseline = "cpm_ensemble_512", 5, 3, True
+            torch.cuda.empty_cache()
+            el = ensemble_measure(ea, 1, 0, local, None)
+            line["ensemble"] = {k: el[k] for k in ("metric", "value", "unit", "ms_per_step", "steps", "warmup",
+                                                   "config", "roofline", "e2e", "gpu_launches", "clocks")}
+        except Exception as exc:  # reported, not fatal
+            line["ensemble"] = {"error": "%s: %s" % (type(exc).__name__, exc)}
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
@@ -493,13 +506,24 @@ def _oracle_replica(job):
 def run_gpu_batch(args):
     import torch
     from paper_2312_09317_gb300 import build as B
-    from paper_2312_09317_gb300 import cpm
 
     ws_, rank, local, dist = dist_init()
     torch.cuda.set_device(local)
     if rank == 0 or not os.path.exists(B.LIB):
         B.build()
     barrier(dist)
+    line = ensemble_measure(args, ws_, rank, local, dist)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def ensemble_measure(args, ws_, rank, local, dist):
+    """One ensemble workload's line (rank 0; None on the other ranks)."""
+    import torch
+    from paper_2312_09317_gb300 import cpm
     factory, desc = ENSEMBLES[args.workload]
     members = [w.replace(seed=w.seed + 1000003 * rank) for w in factory()]
     stream = torch.cuda.Stream()
@@ -604,12 +628,9 @@ def run_gpu_batch(args):
             "gpu_launches": int(launches),
             "clocks": clk,
         }
-        print(json.dumps(line))
     for b in batches:
         b.close()
-    if dist is not None:
-        dist.destroy_process_group()
-    return 0
+    return line if rank == 0 else None
 
 
 def run_emulator_sweep(args):
@@ -779,8 +800,10 @@ def main():
                     "region (default: a temporary file)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--loop", default="persistent", choices=["persistent", "graph"],
-                    help="ensembles: one persistent cooperative launch per step, or one CUDA graph per MCS")
+    ap.add_argument("--loop", default="graph", choices=["persistent", "graph"],
+                    help="ensembles: one CUDA graph per MCS (faster on GB300), or one persistent cooperative "
+                         "launch per step")
+    ap.add_argument("--no-ensemble", action="store_true", help="default workload: skip the embedded ensemble line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -61,6 +61,12 @@ __device__ __forceinline__ void around(uint32_t x, uint32_t n, uint32_t out[3])
     out[2] = x + 1 == n ? 0 : x + 1;
 }
 
+// x + d (d in -1, 0, 1) on a periodic axis of extent n, for x in [0, n)
+__device__ __forceinline__ uint32_t wrap_step(uint32_t x, int d, uint32_t n)
+{
+    return d < 0 ? (x == 0 ? n - 1 : x - 1) : (d > 0 ? (x + 1 == n ? 0 : x + 1) : x);
+}
+
 // A lattice word of the round kernels.  With Act and areas of edge 8 or
 // more, through the streaming cache path (ld.global.cs, evict first): the
 // active blocks of a round are then 8 sites apart, a round touches each
@@ -92,19 +98,16 @@ __device__ int64_t gm_q(const RoundArgs &a, const SmemTables &sm, uint32_t x, ui
                         int max_act)
 {
     if (sigma <= 0) return 0;
-    uint32_t xs[3], ys[3], zs[3];
-    around(x, a.nx, xs);
-    around(y, a.ny, ys);
-    if (DIM == 3) around(z, a.nz, zs); else zs[0] = zs[1] = zs[2] = 0;
     int32_t sum = 0, cnt = 0;
 #pragma unroll(ROLL >= 1 ? 1 : 3)
     for (int dz = (DIM == 3 ? 0 : 1); dz < (DIM == 3 ? 3 : 2); ++dz) {
+        const uint32_t zz = DIM == 3 ? wrap_step(z, dz - 1, a.nz) : 0;
 #pragma unroll(ROLL >= 2 ? 1 : 3)
         for (int dy = 0; dy < 3; ++dy) {
-            const uint32_t row = a.nx * (ys[dy] + a.ny * zs[dz]);
+            const uint32_t row = a.nx * (wrap_step(y, dy - 1, a.ny) + a.ny * zz);
 #pragma unroll
             for (int dx = 0; dx < 3; ++dx) {
-                const uint32_t site = xs[dx] + row;
+                const uint32_t site = wrap_step(x, dx - 1, a.nx) + row;
                 const bool centre = dx == 1 && dy == 1 && dz == 1;
                 const int32_t w = lat_word<true>(a, site);
                 if (!centre && cell_id(w) != sigma) continue;
@@ -202,12 +205,12 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
         const uint32_t idx = n + (n >= NB / 2 ? 1u : 0u);  // skip the centre of the 3^d stencil
         const int ox = (int)(idx % 3), oy = (int)((idx / 3) % 3), oz = DIM == 3 ? (int)(idx / 9) : 1;
 
-        uint32_t xs[3], ys[3], zs[3];
-        around(jx, a.nx, xs);
-        around(jy, a.ny, ys);
-        if (DIM == 3) around(jz, a.nz, zs); else zs[0] = zs[1] = zs[2] = 0;
+        // wrapped coordinates are computed, not indexed from small arrays: an array
+        // indexed by a run-time value would live in local memory
         const uint32_t j = jx + a.nx * (jy + a.ny * jz);
-        const uint32_t isite = xs[ox] + a.nx * (ys[oy] + a.ny * zs[oz]);
+        const uint32_t ix_ = wrap_step(jx, ox - 1, a.nx), iy_ = wrap_step(jy, oy - 1, a.ny);
+        const uint32_t iz_ = DIM == 3 ? wrap_step(jz, oz - 1, a.nz) : 0;
+        const uint32_t isite = ix_ + a.nx * (iy_ + a.ny * iz_);
         const int32_t sj = cell_id(lat_word<ACT>(a, j));
         const int32_t si = cell_id(lat_word<ACT>(a, isite));
 
@@ -220,13 +223,14 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
                 int mi = 0, mj = 0;
 #pragma unroll(ROLL >= 1 ? 1 : 3)
                 for (int dz = (DIM == 3 ? 0 : 1); dz < (DIM == 3 ? 3 : 2); ++dz) {
+                    const uint32_t zz = DIM == 3 ? wrap_step(jz, dz - 1, a.nz) : 0;
 #pragma unroll(ROLL >= 2 ? 1 : 3)
                     for (int dy = 0; dy < 3; ++dy) {
-                        const uint32_t row = a.nx * (ys[dy] + a.ny * zs[dz]);
+                        const uint32_t row = a.nx * (wrap_step(jy, dy - 1, a.ny) + a.ny * zz);
 #pragma unroll
                         for (int dx = 0; dx < 3; ++dx) {
                             if (dx == 1 && dy == 1 && dz == 1) continue;
-                            const int32_t sn = cell_id(lat_word<ACT>(a, xs[dx] + row));
+                            const int32_t sn = cell_id(lat_word<ACT>(a, wrap_step(jx, dx - 1, a.nx) + row));
                             const int tn = type_of(sn, a.cell_type, a.tp.obstacle_type);
                             if (sn != si) adhesion += sm.J[ti * kMaxTypes + tn]; else ++mi;
                             if (sn != sj) adhesion -= sm.J[tj * kMaxTypes + tn]; else ++mj;
@@ -266,7 +270,6 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
                         if (hi <= 0) decided = 1;
                         else if (lo >= a.L || (lo > 0 && w.v[2] >= __ldg(a.thr + lo))) decided = 0;
                         else {
-                            const uint32_t ix_ = xs[ox], iy_ = ys[oy], iz_ = zs[oz];
                             int64_t gi = 0, gj = 0;
                             if (ROLL >= 2) {
                                 // source then target through one copy of the code
