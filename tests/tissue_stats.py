@@ -15,16 +15,19 @@ displacement of cell centroids over 10 and 50 MCS (all windows of that lag
 inside the observation window).
 """
 import numpy as np
-import torch
 
 N = 128
 BURN, SNAPS, EVERY = 100, 40, 10
 STATS = ("vmean", "vvar", "amean", "acc", "msd10", "msd50")
 
 
-def centroids(lat: torch.Tensor, n_cells: int) -> torch.Tensor:
+def centroids(lat, n_cells: int):
     """Periodic centroid of every cell id 0..n_cells (circular mean along
-    each axis) of a (nz, ny, nx) int32 lattice, float64 [n_cells + 1, 3]."""
+    each axis) of a (nz, ny, nx) int32 lattice (torch tensor on any device,
+    or numpy array), float64 [n_cells + 1, 3] of the same kind."""
+    if isinstance(lat, np.ndarray):
+        return _centroids_np(lat, n_cells)
+    import torch
     ids = lat.reshape(-1).long()
     m = ids > 0
     idx = torch.nonzero(m).squeeze(1)
@@ -43,23 +46,42 @@ def centroids(lat: torch.Tensor, n_cells: int) -> torch.Tensor:
     return out
 
 
+def _centroids_np(lat: np.ndarray, n_cells: int) -> np.ndarray:
+    ids = lat.reshape(-1).astype(np.int64)
+    idx = np.nonzero(ids > 0)[0]
+    ids = ids[idx]
+    out = np.zeros((n_cells + 1, 3))
+    stride = 1
+    for axis in (2, 1, 0):
+        L = lat.shape[axis]
+        coord = (idx // stride) % L
+        stride *= L
+        ang = coord * (2 * np.pi / L)
+        cs = np.bincount(ids, weights=np.cos(ang), minlength=n_cells + 1)
+        sn = np.bincount(ids, weights=np.sin(ang), minlength=n_cells + 1)
+        out[:, axis] = np.remainder(np.arctan2(sn, cs), 2 * np.pi) * (L / (2 * np.pi))
+    return out
+
+
 class Recorder:
     """Accumulates one run's snapshots: centroids (unwrapped across
     snapshots by the minimal image), tallies and the accepted-copy count."""
 
     def __init__(self, shape, n_cells: int):
-        self.L = torch.tensor(shape, dtype=torch.float64)
+        self.L = np.array(shape, dtype=np.float64)
         self.n_cells = n_cells
         self.traj, self.prev = [], None
         self.V, self.A = [], []
 
-    def snapshot(self, lat: torch.Tensor, V=None, A=None):
-        c = centroids(lat, self.n_cells).cpu()
+    def snapshot(self, lat, V=None, A=None):
+        c = centroids(lat, self.n_cells)
+        if not isinstance(c, np.ndarray):
+            c = c.cpu().numpy()
         if self.prev is None:
-            self.traj.append(torch.zeros_like(c))
+            self.traj.append(np.zeros_like(c))
         else:
             d = c - self.prev
-            d -= torch.round(d / self.L) * self.L
+            d -= np.round(d / self.L) * self.L
             self.traj.append(self.traj[-1] + d)
         self.prev = c
         if V is not None:
@@ -67,7 +89,7 @@ class Recorder:
             self.A.append(np.asarray(A, dtype=np.float64)[1:])
 
     def summary(self, accepts: int, n_sites: int) -> dict:
-        traj = torch.stack(self.traj)[:, 1:, :].numpy()
+        traj = np.stack(self.traj)[:, 1:, :]
         V, A = np.array(self.V), np.array(self.A)
         live = V > 0
         lag = lambda k: float(((traj[k:] - traj[:-k]) ** 2).sum(-1).mean())
