@@ -507,12 +507,13 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, lon
 template <int DIM, bool PERIM, bool ACT>
 __global__ void __launch_bounds__(kBatchMaxThreads, ACT ? CPM_BATCH_MIN_BLOCKS_ACT : CPM_BATCH_MIN_BLOCKS)
     batch_loop_kernel(BatchLattice *lats, uint32_t n_lats, const int2 *items, const uint32_t *upto_q, uint32_t r_max,
-                      const int2 *clamp, uint32_t n_clamp, uint32_t n_mcs, unsigned *bar, long long max_polls,
-                      int *err, int test_absent)
+                      const int2 *clamp, uint32_t n_clamp, uint32_t n_mcs, unsigned *bar, unsigned *next,
+                      long long max_polls, int *err, int test_absent)
 {
     __shared__ RoundArgs ra;
     __shared__ SmemTables sm;
     __shared__ int ok_s;
+    __shared__ uint32_t claim_s;
     // test of the timeout path: the first CTA never arrives, so the others' first barrier wait runs out
     if (test_absent && blockIdx.x == 0) return;
     unsigned target = 0;
@@ -524,16 +525,26 @@ __global__ void __launch_bounds__(kBatchMaxThreads, ACT ? CPM_BATCH_MIN_BLOCKS_A
         }
         for (uint32_t q = 0; q < r_max; ++q) {
             const uint32_t n_items = upto_q[q];
-            for (uint32_t k = blockIdx.x; k < n_items; k += gridDim.x)
+            // items are claimed one at a time from the round's counter, so that CTAs that drew cheap items
+            // take more of them (a fixed grid-stride split leaves the round waiting for the unluckiest CTA)
+            for (;;) {
+                __syncthreads();
+                if (threadIdx.x == 0) claim_s = atomicAdd(next + q, 1u);
+                __syncthreads();
+                const uint32_t k = claim_s;
+                if (k >= n_items) break;
                 batch_round_item<DIM, PERIM, ACT>(ra, sm, lats, items[k], q);
+            }
             target += gridDim.x;
             if (!grid_barrier(bar, target, max_polls, err, ok_s)) return;
         }
-        if (blockIdx.x == 0)
+        if (blockIdx.x == 0) {
             for (uint32_t l = threadIdx.x; l < n_lats; l += blockDim.x) {
                 lats[l].t_start += 1;
                 lats[l].g_start += lats[l].R;
             }
+            for (uint32_t q = threadIdx.x; q < r_max; q += blockDim.x) next[q] = 0;  // the next MCS claims anew
+        }
         target += gridDim.x;
         if (!grid_barrier(bar, target, max_polls, err, ok_s)) return;
     }
@@ -678,10 +689,12 @@ cudaError_t launch_batch_loop_t(const BatchLoopArgs &p, uint32_t threads, cudaSt
     const int2 *items = p.items, *clamp = p.clamp;
     const uint32_t *upto = p.upto_q;
     unsigned *bar = p.bar;
+    unsigned *next = p.next;
     long long polls = p.max_polls;
     int *err = p.err;
     int absent = p.test_absent;
-    void *args[] = {&lats, &n_lats, &items, &upto, &r_max, &clamp, &n_clamp, &n_mcs, &bar, &polls, &err, &absent};
+    void *args[] = {&lats, &n_lats, &items, &upto, &r_max, &clamp, &n_clamp, &n_mcs, &bar, &next, &polls, &err,
+                    &absent};
     return cudaLaunchCooperativeKernel((const void *)kern, dim3((unsigned)grid), dim3(threads), args, 0, st);
 }
 
