@@ -218,11 +218,12 @@ int reset_tallies(cpm_handle *h)
     return CPM_OK;
 }
 
-// Staging buffer of up to 4 Mi words for host reads and loads of a packed lattice.
+// Staging buffer of up to 64 Mi words (256 MiB) for host reads and loads of a
+// packed lattice: large enough that each chunk's copy runs at the link's speed.
 int ensure_stage(cpm_handle *h)
 {
     if (h->stage) return CPM_OK;
-    const uint64_t n = std::min<uint64_t>(h->n_sites, (uint64_t)1 << 22);
+    const uint64_t n = std::min<uint64_t>(h->n_sites, (uint64_t)1 << 26);
     CUDA_TRY(h, cudaMalloc(&h->stage, sizeof(int32_t) * n));
     h->stage_n = n;
     return CPM_OK;
