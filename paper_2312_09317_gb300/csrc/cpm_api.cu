@@ -915,7 +915,7 @@ struct cpm_batch {
     long long max_polls = 1ll << 24;     // bound of each grid-barrier wait (polls about 100 ns apart)
     uint32_t *d_upto_q = nullptr;        // round items per round q
     uint32_t r_max_items = 0;            // items of the fullest round
-    unsigned *d_bar = nullptr;           // barrier counter
+    unsigned long long *d_bar = nullptr; // barrier counter
     unsigned *d_next = nullptr;          // per-round item counters of the persistent loop
     int *d_err = nullptr;                // barrier timeout flag
     uint32_t loop_grid = 0;              // CTAs of the last persistent launch
@@ -1216,7 +1216,7 @@ int cpm_batch_step(cpm_batch *b, int64_t n_mcs)
             p.max_items = b->r_max_items;
             p.test_absent = b->test_absent ? 1 : 0;
             p.next = b->d_next;
-            cudaError_t e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned), b->stream);
+            cudaError_t e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned long long), b->stream);
             if (e == cudaSuccess) e = cudaMemsetAsync(b->d_next, 0, sizeof(unsigned) * p.r_max, b->stream);
             if (e == cudaSuccess) e = launch_batch_loop(b->dim, b->perim, b->act, p, batch_threads(b), b->stream,
                                                         &b->loop_grid);
@@ -1255,7 +1255,7 @@ int cpm_batch_set_persistent(cpm_batch *b, int32_t on, int64_t max_polls)
 {
     if (!b) return CPM_E_HANDLE;
     if (on && !b->d_bar) {
-        cudaError_t e = cudaMalloc(&b->d_bar, sizeof(unsigned));
+        cudaError_t e = cudaMalloc(&b->d_bar, sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMalloc(&b->d_next, sizeof(unsigned) * std::max<uint32_t>(1u, b->lats[b->order[0]].R));
         if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);

@@ -140,7 +140,7 @@ struct BatchLoopArgs {
     const int2 *clamp;        // Act clamp items
     uint32_t n_clamp;
     uint32_t n_mcs;
-    unsigned *bar;            // grid barrier counter, 0 at launch
+    unsigned long long *bar;  // grid barrier counter, 0 at launch
     unsigned *next;           // per round: items claimed so far (r_max counters, 0 at launch)
     long long max_polls;      // bound of every barrier wait
     int *err;                 // set to 1 when a wait runs out

@@ -463,23 +463,25 @@ __device__ __forceinline__ void batch_clamp_item(const BatchLattice *lats, int2 
 }
 
 
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long *p)
 {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
-// Grid-wide barrier of a co-resident (cooperative) grid on a counter that
-// starts at 0: the k-th barrier waits for k * gridDim.x arrivals.  The wait
-// is bounded: after max_polls polls (about 100 ns apart) the CTA records the
-// timeout in *err and the barrier returns false; the caller then returns.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, long long max_polls, int *err, int &ok_s)
+// Grid-wide barrier of a co-resident (cooperative) grid on a 64-bit counter
+// that starts at 0 (a call may pass billions of arrivals): the k-th barrier
+// waits for k * gridDim.x arrivals.  The wait is bounded: after max_polls
+// polls (about 100 ns apart) the CTA records the timeout in *err and the
+// barrier returns false; the caller then returns.
+__device__ __forceinline__ bool grid_barrier(unsigned long long *bar, unsigned long long target, long long max_polls,
+                                             int *err, int &ok_s)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        atomicAdd(bar, 1u);
+        atomicAdd(bar, 1ull);
         int ok = 1;
         long long polls = 0;
         while (ld_acquire_gpu(bar) < target) {
@@ -507,7 +509,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, lon
 template <int DIM, bool PERIM, bool ACT>
 __global__ void __launch_bounds__(kBatchMaxThreads, ACT ? CPM_BATCH_MIN_BLOCKS_ACT : CPM_BATCH_MIN_BLOCKS)
     batch_loop_kernel(BatchLattice *lats, uint32_t n_lats, const int2 *items, const uint32_t *upto_q, uint32_t r_max,
-                      const int2 *clamp, uint32_t n_clamp, uint32_t n_mcs, unsigned *bar, unsigned *next,
+                      const int2 *clamp, uint32_t n_clamp, uint32_t n_mcs, unsigned long long *bar, unsigned *next,
                       long long max_polls, int *err, int test_absent)
 {
     __shared__ RoundArgs ra;
@@ -516,7 +518,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, ACT ? CPM_BATCH_MIN_BLOCKS_A
     __shared__ uint32_t claim_s;
     // test of the timeout path: the first CTA never arrives, so the others' first barrier wait runs out
     if (test_absent && blockIdx.x == 0) return;
-    unsigned target = 0;
+    unsigned long long target = 0;
     for (uint32_t m = 0; m < n_mcs; ++m) {
         if (ACT) {
             for (uint32_t c = blockIdx.x; c < n_clamp; c += gridDim.x) batch_clamp_item(lats, clamp[c]);
@@ -688,7 +690,7 @@ cudaError_t launch_batch_loop_t(const BatchLoopArgs &p, uint32_t threads, cudaSt
     uint32_t n_lats = p.n_lats, r_max = p.r_max, n_clamp = p.n_clamp, n_mcs = p.n_mcs;
     const int2 *items = p.items, *clamp = p.clamp;
     const uint32_t *upto = p.upto_q;
-    unsigned *bar = p.bar;
+    unsigned long long *bar = p.bar;
     unsigned *next = p.next;
     long long polls = p.max_polls;
     int *err = p.err;
