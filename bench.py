@@ -55,9 +55,11 @@ WORKLOADS = {
                           .format(**cw.TISSUE_SCHEDULE)),
     "cpm3d_tissue_512": (lambda: cw.fibre_tissue_3d(seed=1, n=512, device="cuda", **cw.TISSUE_SCHEDULE), 10,
                          "3D tissue 512^3, otherwise as cpm3d_tissue_1024"),
-    # the paper's smaller areas (4^3, 2x2x2 checkerboard): faster, but biased against the serial chain
+    # smaller areas: faster, but biased against the serial chain (the paper's 4^3, and 8^3)
     "cpm3d_tissue_1024_a4": (lambda: cw.fibre_tissue_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda"), 10,
                              "as cpm3d_tissue_1024 with a=4, c=2, P=8"),
+    "cpm3d_tissue_1024_a8": (lambda: cw.fibre_tissue_3d(seed=1, n=1024, a=8, c=2, P=64, device="cuda"), 10,
+                             "as cpm3d_tissue_1024 with a=8, c=2, P=64"),
     # the tissue workload under the tiled schedule (tiles of edge 16, one tile cycle per MCS)
     "cpm3d_tissue_1024_tiled": (lambda: cw.fibre_tissue_3d(seed=1, n=1024, a=4, c=2, P=8, device="cuda")
                                 .replace(tile=16, tile_cycles=1), 10,

@@ -212,13 +212,16 @@ def test_tissue_64_bit_exact(cpm):
 
 
 def test_tissue_1024_sampled(cpm):
-    """1024^3 tissue workload in the launch configuration bench.py times
-    (cpm_workloads.TISSUE_SCHEDULE: one round per sub-pass).  After 2 MCS and 3 sub-passes,
+    """1024^3 tissue workload in the launch configuration bench.py times: the
+    areas of cpm_workloads.TISSUE_SCHEDULE (the same grid of active blocks and
+    CTAs), with one round per sub-pass so that a single round can be replayed
+    for sampled blocks.  After 2 MCS and 3 sub-passes,
     one more round runs on the GPU; the oracle replays that round for 4,096
     sampled active blocks from the GPU's state before it, and their sites and
     Act values must match.  Tallies are checked at full size by a device
     recount, obstacles by comparison with the input."""
-    w = cw.fibre_tissue_3d(seed=1, n=1024, device="cuda", **cw.TISSUE_SCHEDULE)
+    a, c = cw.TISSUE_SCHEDULE["a"], cw.TISSUE_SCHEDULE["c"]
+    w = cw.fibre_tissue_3d(seed=1, n=1024, device="cuda", a=a, c=c, P=(a // c) ** 3)
     assert (w.a // w.c) ** 3 // w.P == 1  # one round per sub-pass: the sampled round is the whole sub-pass
     sim = cpm.Sim(w)
     sim.step(2)
