@@ -108,13 +108,11 @@ DEFAULT_WORKLOAD = "cpm3d_tissue_1024"
 
 # DRAM bytes per round-kernel launch from the last ncu capture, valid only for
 # the kernel source it was taken on (sha1 of csrc/cpm_kernels.cu, first 12 hex).
-# The 1024^3 tissue launch is too large to capture; its figure is the 512^3
-# capture after the growth burn-in (102.05 MB read + 5.72 MB written per launch
-# of 262,144 attempts) scaled by the 8x sites: a round makes one attempt per
-# active block, all over the lattice, so traffic grows with the sites.
+# Both are single-pass captures (dram__bytes_read/write.sum) of one launch after
+# the growth burn-in and the warm-up, the 1024^3 one at full size.
 NCU_TRAFFIC = {
-    ("cpm3d_tissue_1024", "8580215559dc"): 8 * (102.053376e6 + 5.722624e6),
-    ("cpm3d_tissue_512", "8580215559dc"): 102.053376e6 + 5.722624e6,
+    ("cpm3d_tissue_1024", "ef95fe722afd"): 131.86e6 + 7.15e6,
+    ("cpm3d_tissue_512", "ef95fe722afd"): 15.64e6 + 2.30e3,
 }
 
 
