@@ -108,11 +108,10 @@ DEFAULT_WORKLOAD = "cpm3d_tissue_1024"
 
 # DRAM bytes per round-kernel launch from the last ncu capture, valid only for
 # the kernel source it was taken on (sha1 of csrc/cpm_kernels.cu, first 12 hex).
-# Both are single-pass captures (dram__bytes_read/write.sum) of one launch after
-# the growth burn-in and the warm-up, the 1024^3 one at full size.
+# A single-pass capture (dram__bytes_read/write.sum) of one launch at full size,
+# after the growth burn-in and the warm-up.
 NCU_TRAFFIC = {
-    ("cpm3d_tissue_1024", "ef95fe722afd"): 131.86e6 + 7.15e6,
-    ("cpm3d_tissue_512", "ef95fe722afd"): 15.64e6 + 2.30e3,
+    ("cpm3d_tissue_1024", "9d07898d5831"): 131.75e6 + 7.51e6,
 }
 
 

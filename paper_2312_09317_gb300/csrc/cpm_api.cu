@@ -254,6 +254,7 @@ int run_subpass(cpm_handle *h)
     a.lat = h->lat;
     a.packed = h->act ? 1u : 0u;
     a.stream_loads = h->act && h->cfg.a >= 8 ? 1u : 0u;
+    a.pdl = 1;  // each round overlaps its set-up with the previous round's tail
     a.cell_type = h->cell_type;
     a.thr = h->thr;
     a.ln_tab = h->ln_tab;

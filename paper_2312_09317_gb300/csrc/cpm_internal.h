@@ -86,6 +86,7 @@ struct RoundArgs {
     int32_t *lat;              // lattice words (see cell_id), x fastest
     uint32_t packed;           // 1: the words carry Act stamps (Act on for this lattice)
     uint32_t stream_loads;     // 1: lattice words through the streaming cache path (Act, area edge >= 8)
+    uint32_t pdl;              // 1: launched as a programmatic dependent of the previous round
     const uint8_t *cell_type;  // per cell id
     const int32_t *Vc, *Ac;    // tallies as of the start of this round
     int32_t *Vn, *An;          // tallies being built for the next round

@@ -185,12 +185,6 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
 {
     constexpr int NB = DIM == 3 ? 26 : 8;
     bool accepted = false;
-        // the previous round's accepted change goes into the next tallies
-        if (a.flag_prev[i]) {
-            const int4 e = a.pend_prev[i];
-            if (e.x > 0) { atomicAdd(a.Vn + e.x, 1); atomicAdd(a.An + e.x, e.z); }
-            if (e.y > 0) { atomicAdd(a.Vn + e.y, -1); atomicAdd(a.An + e.y, e.w); }
-        }
 
         // the active block of this thread
         const uint32_t bx = ix * a.c + a.cx, by = iy * a.c + a.cy, bz = DIM == 3 ? iz * a.c + a.cz : 0;
@@ -211,6 +205,17 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
         const uint32_t ix_ = wrap_step(jx, ox - 1, a.nx), iy_ = wrap_step(jy, oy - 1, a.ny);
         const uint32_t iz_ = DIM == 3 ? wrap_step(jz, oz - 1, a.nz) : 0;
         const uint32_t isite = ix_ + a.nx * (iy_ + a.ny * iz_);
+
+        // everything above depends on the launch arguments only; the lattice, flags and
+        // tallies below are the previous round's output, so a round launched as a
+        // programmatic dependent of the previous one waits for it here
+        if (a.pdl) asm volatile("griddepcontrol.wait;" ::: "memory");
+        // the previous round's accepted change goes into the next tallies
+        if (a.flag_prev[i]) {
+            const int4 e = a.pend_prev[i];
+            if (e.x > 0) { atomicAdd(a.Vn + e.x, 1); atomicAdd(a.An + e.x, e.z); }
+            if (e.y > 0) { atomicAdd(a.Vn + e.y, -1); atomicAdd(a.An + e.y, e.w); }
+        }
         const int32_t sj = cell_id(lat_word<ACT>(a, j));
         const int32_t si = cell_id(lat_word<ACT>(a, isite));
 
@@ -323,6 +328,9 @@ __global__ void __launch_bounds__(kThreads, ACT ? CPM_ROUND_MIN_BLOCKS_ACT : CPM
     round_kernel(const RoundArgs a)
 {
     __shared__ SmemTables sm;
+    // the next round may place its CTAs on free SM slots from now on; they compute
+    // their sites and random numbers, then wait for this round to finish
+    if (a.pdl) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     load_tables(sm, a, ACT);
     __syncthreads();
 
@@ -629,8 +637,24 @@ cudaError_t launch_round_t(const RoundArgs &a, cudaStream_t st)
     const unsigned blocks = ((a.nax + a.brick_x - 1) / a.brick_x) * ((a.nay + a.brick_y - 1) / a.brick_y) *
                             ((naz + bz - 1) / bz);
     const unsigned threads = a.brick_x * a.brick_y * bz;
-    round_kernel<DIM, PERIM, ACT><<<blocks, threads, 0, st>>>(a);
-    return cudaGetLastError();
+    if (!a.pdl) {
+        round_kernel<DIM, PERIM, ACT><<<blocks, threads, 0, st>>>(a);
+        return cudaGetLastError();
+    }
+    // programmatic dependent launch: the CTAs of this round may start while the
+    // previous kernel of the stream drains (it allows it once all its CTAs have
+    // started); they wait for its completion before they touch the lattice
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, round_kernel<DIM, PERIM, ACT>, a);
 }
 
 }  // namespace

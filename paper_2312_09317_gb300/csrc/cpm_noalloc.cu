@@ -185,6 +185,7 @@ extern "C" int cpm_step_noalloc(const cpm_config *cfg, int32_t *lattice, int32_t
     memset(&a, 0, sizeof a);
     a.lat = lattice;
     a.packed = 0;  // no Act term here: the words are plain ids
+    a.pdl = 1;     // each round overlaps its set-up with the previous round's tail
     a.cell_type = cell_type;
     a.thr = d_thr;
     a.ln_tab = d_ln;
