@@ -111,7 +111,7 @@ DEFAULT_WORKLOAD = "cpm3d_tissue_1024"
 # A single-pass capture (dram__bytes_read/write.sum) of one launch at full size,
 # after the growth burn-in and the warm-up.
 NCU_TRAFFIC = {
-    ("cpm3d_tissue_1024", "9d07898d5831"): 131.75e6 + 7.51e6,
+    ("cpm3d_tissue_1024", "85527150aca0"): 132.13e6 + 8.02e6,
 }
 
 

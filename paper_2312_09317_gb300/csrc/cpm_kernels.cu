@@ -169,16 +169,20 @@ __device__ __noinline__ int64_t motility_q(const RoundArgs &a, int32_t si, int32
 // described by a; also carries the previous round's change of index i into
 // the next tallies.  Returns whether the copy was accepted.
 //
+// The target's Act geometric mean (Eq. 9) is gathered in the neighbour sum,
+// which reads the same 3^3 window around the target; only the source's mean
+// reads a window of its own, and only when the Act term decides the test.
+//
 // ROLL is a code-size level.  The fully unrolled stencil loops make the Act
 // kernels large enough that instruction fetch stalls them (a warp's lanes sit
 // in different phases of the attempt), so those kernels roll loops from the
 // outside in: level 1 (single-lattice Act kernels, batched 2D Act kernel)
-// rolls the outer (z) loops of the neighbour sum and of the geometric mean;
-// level 2 (batched 3D Act kernel, whose CTAs mix lattices) also rolls the
-// middle (y) loops and runs the two geometric means through one copy of the
-// code.  Level 0 (kernels without Act) stays fully unrolled.  The level
-// changes only the code layout: every sum visits the same sites in the same
-// order.
+// rolls the outer (z) loop of the neighbour sum and keeps the source's
+// geometric mean unrolled (its 27 loads issue together); level 2 (batched 3D
+// Act kernel, whose CTAs mix lattices) also rolls the middle (y) loop and
+// rolls the geometric mean like the neighbour sum.  Level 0 (kernels without
+// Act) stays fully unrolled.  The level changes only the code layout: every
+// sum visits the same sites, and integer sums do not depend on the order.
 template <int DIM, bool PERIM, bool ACT, int ROLL>
 __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTables &sm, uint32_t ix, uint32_t iy,
                                               uint32_t iz, uint32_t i)
@@ -216,7 +220,8 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
             if (e.x > 0) { atomicAdd(a.Vn + e.x, 1); atomicAdd(a.An + e.x, e.z); }
             if (e.y > 0) { atomicAdd(a.Vn + e.y, -1); atomicAdd(a.An + e.y, e.w); }
         }
-        const int32_t sj = cell_id(lat_word<ACT>(a, j));
+        const int32_t wj = lat_word<ACT>(a, j);
+        const int32_t sj = cell_id(wj);
         const int32_t si = cell_id(lat_word<ACT>(a, isite));
 
         if (si != sj && si >= 0 && sj >= 0) {
@@ -226,6 +231,14 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
                 const int tj = type_of(sj, a.cell_type, a.tp.obstacle_type);
                 int32_t adhesion = 0;
                 int mi = 0, mj = 0;
+                // target's Act log-sum over its same-cell 3^3 window (centre first), gathered in
+                // the neighbour sum; negative once a zero Act value is met (the mean is then 0)
+                const int maxj = ACT && sj > 0 ? (int)sm.ma[tj] : 0;
+                int32_t lsj = 0;
+                if (ACT) {
+                    const int v = act_value(word_stamp(wj), a.t & 255u, maxj);
+                    lsj = v == 0 ? INT32_MIN / 2 : (int32_t)sm.ln[v];
+                }
 #pragma unroll(ROLL >= 1 ? 1 : 3)
                 for (int dz = (DIM == 3 ? 0 : 1); dz < (DIM == 3 ? 3 : 2); ++dz) {
                     const uint32_t zz = DIM == 3 ? wrap_step(jz, dz - 1, a.nz) : 0;
@@ -235,10 +248,18 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
 #pragma unroll
                         for (int dx = 0; dx < 3; ++dx) {
                             if (dx == 1 && dy == 1 && dz == 1) continue;
-                            const int32_t sn = cell_id(lat_word<ACT>(a, wrap_step(jx, dx - 1, a.nx) + row));
+                            const int32_t wn = lat_word<ACT>(a, wrap_step(jx, dx - 1, a.nx) + row);
+                            const int32_t sn = cell_id(wn);
                             const int tn = type_of(sn, a.cell_type, a.tp.obstacle_type);
                             if (sn != si) adhesion += sm.J[ti * kMaxTypes + tn]; else ++mi;
-                            if (sn != sj) adhesion -= sm.J[tj * kMaxTypes + tn]; else ++mj;
+                            if (sn != sj) adhesion -= sm.J[tj * kMaxTypes + tn];
+                            else {
+                                ++mj;
+                                if (ACT) {
+                                    const int v = act_value(word_stamp(wn), a.t & 255u, maxj);
+                                    lsj = v == 0 ? INT32_MIN / 2 : lsj + (int32_t)sm.ln[v];
+                                }
+                            }
                         }
                     }
                 }
@@ -275,22 +296,12 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
                         if (hi <= 0) decided = 1;
                         else if (lo >= a.L || (lo > 0 && w.v[2] >= __ldg(a.thr + lo))) decided = 0;
                         else {
-                            int64_t gi = 0, gj = 0;
-                            if (ROLL >= 2) {
-                                // source then target through one copy of the code
-#pragma unroll 1
-                                for (int q = 0; q < 2; ++q) {
-                                    const bool src = q == 0;
-                                    const int64_t g =
-                                        gm_q<DIM, ROLL>(a, sm, src ? ix_ : jx, src ? iy_ : jy, src ? iz_ : jz,
-                                                        src ? si : sj,
-                                                        src ? (si > 0 ? sm.ma[ti] : 0) : (sj > 0 ? sm.ma[tj] : 0));
-                                    if (src) gi = g; else gj = g;
-                                }
-                            } else {
-                                gi = gm_q<DIM, ROLL>(a, sm, ix_, iy_, iz_, si, si > 0 ? sm.ma[ti] : 0);
-                                gj = gm_q<DIM, ROLL>(a, sm, jx, jy, jz, sj, sj > 0 ? sm.ma[tj] : 0);
-                            }
+                            // target: the log-sum gathered above over the sites gm_q would visit
+                            // (the centre and the mj same-cell neighbours)
+                            const int64_t gj =
+                                sj > 0 && lsj >= 0 ? (int64_t)__ldg(a.expq + ((lsj / (mj + 1)) >> 6)) : 0;
+                            const int64_t gi = gm_q<DIM, (ROLL >= 2 ? ROLL : 0)>(a, sm, ix_, iy_, iz_, si,
+                                                                                 si > 0 ? sm.ma[ti] : 0);
                             dhq += floor_div_pos(lam * (gj - gi), mx * 4096);
                         }
                     }
