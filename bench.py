@@ -107,17 +107,20 @@ BURN_IN = {"cpm2d_200": 50, "cpm3d_256": 50, "cpm3d_512": 50, "cpm3d_tissue_1024
 DEFAULT_WORKLOAD = "cpm3d_tissue_1024"
 
 # DRAM bytes per round-kernel launch from the last ncu capture, valid only for
-# the kernel source it was taken on (sha1 of csrc/cpm_kernels.cu, first 12 hex).
-# A single-pass capture (dram__bytes_read/write.sum) of one launch at full size,
-# after the growth burn-in and the warm-up.
+# the kernel source and launch shapes it was taken on (sha1 of csrc/cpm_kernels.cu
+# followed by csrc/cpm_internal.h, first 12 hex).  A single-pass capture
+# (dram__bytes_read/write.sum) of one launch at full size, after the growth
+# burn-in and the warm-up.
 NCU_TRAFFIC = {
-    ("cpm3d_tissue_1024", "85527150aca0"): 132.13e6 + 8.02e6,
+    ("cpm3d_tissue_1024", "ba609db67c41"): 131.37e6 + 7.97e6,
 }
 
 
 def kernel_hash() -> str:
-    p = os.path.join(ROOT, "paper_2312_09317_gb300", "csrc", "cpm_kernels.cu")
-    return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12]
+    h = hashlib.sha1()
+    for f in ("cpm_kernels.cu", "cpm_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2312_09317_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
 
 
 def peaks():
