@@ -68,6 +68,7 @@ class Params(ctypes.Structure):
         ("pers_hist", ctypes.POINTER(ctypes.c_double)),
         ("pers_hist_len", ctypes.c_int32),
         ("pers_t0", ctypes.c_int64),
+        ("csum", ctypes.POINTER(ctypes.c_int64)),
     ]
 
 
@@ -114,6 +115,10 @@ def lib():
                                           i64p, ctypes.c_int64, i64p]
         _lib.orc_tile_offset_of.argtypes = [P(Params), ctypes.c_int64, i64p]
         _lib.orc_tile_offset_of.restype = None
+        _lib.orc_track_init.argtypes = [P(Params), i32p, i32p, i64p]
+        _lib.orc_track_init.restype = None
+        _lib.orc_track_rewrap.argtypes = [P(Params), i32p, i64p]
+        _lib.orc_track_rewrap.restype = None
     return _lib
 
 
@@ -125,7 +130,7 @@ class State:
     """Oracle state for one workload: lattice, Act values, tallies, position.
     Keeps a reference to every array handed to C."""
 
-    def __init__(self, w, act_on=None, recount=True):
+    def __init__(self, w, act_on=None, recount=True, track=False):
         self.w = w
         self.lattice = np.ascontiguousarray(w.lattice, dtype=np.int32).copy()
         self.cell_type = np.ascontiguousarray(w.cell_type, dtype=np.uint8).copy()
@@ -149,6 +154,13 @@ class State:
                               _ptr(self.V, ctypes.c_int32), _ptr(self.A, ctypes.c_int32))
         self.t = 0
         self.sp = 0
+        # composite variable tracking (Eq. 11): per-cell coordinate sums, centroid = S / V
+        self.csum = None
+        if track:
+            self.csum = np.zeros((w.n_cells + 1, 3), dtype=np.int64)
+            self.params.csum = _ptr(self.csum, ctypes.c_int64)
+            lib().orc_track_init(ctypes.byref(self.params), _ptr(self.lattice, ctypes.c_int32),
+                                 _ptr(self.V, ctypes.c_int32), _ptr(self.csum, ctypes.c_int64))
         if pers:  # the centroids at the start: the first look-back point
             lib().orc_pers_update(ctypes.byref(self.params), _ptr(self.lattice, ctypes.c_int32), 0)
         self.rng = (ctypes.c_uint64 * 4)()
@@ -231,6 +243,19 @@ class State:
         lib().orc_motility(ctypes.byref(self.params), _ptr(self.lattice, ctypes.c_int32), j, n_idx,
                            ctypes.byref(q), ctypes.byref(r))
         return q.value, r.value
+
+    def track_sums_of(self, lattice=None) -> np.ndarray:
+        """Coordinate sums (Eq. 11) of a lattice (default: this state's) as
+        tracking starts them, with this state's parameters: [n_cells + 1, 3]."""
+        lat = self.lattice if lattice is None else np.ascontiguousarray(lattice, dtype=np.int32)
+        V = np.zeros(self.w.n_cells + 1, dtype=np.int32)
+        A = np.zeros_like(V)
+        lib().orc_recount(ctypes.byref(self.params), _ptr(lat, ctypes.c_int32), _ptr(V, ctypes.c_int32),
+                          _ptr(A, ctypes.c_int32))
+        S = np.zeros((self.w.n_cells + 1, 3), dtype=np.int64)
+        lib().orc_track_init(ctypes.byref(self.params), _ptr(lat, ctypes.c_int32), _ptr(V, ctypes.c_int32),
+                             _ptr(S, ctypes.c_int64))
+        return S
 
     def centroids(self) -> np.ndarray:
         X = np.zeros((self.w.n_cells + 1, 3))

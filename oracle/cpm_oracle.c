@@ -68,6 +68,8 @@ typedef struct {
     double *pers_hist;          /* state: [pers_hist_len][n_cells + 1][3] centroids, NaN for absent cells */
     int32_t pers_hist_len;      /* > max dt_pers */
     int64_t pers_t0;            /* MCS of the first recorded centroids */
+    /* composite variable tracking (Eq. 11); NULL when off (global schedule only) */
+    int64_t *csum;              /* state: [n_cells + 1][3] coordinate sums of each cell's sites */
 } orc_params;
 
 /* ------------------------------------------------------------------ */
@@ -517,6 +519,69 @@ static int64_t floor_div(int64_t a, int64_t b)
     return q;
 }
 
+/* ------------------------------------------------------------------ */
+/* Composite variable tracking (Methods, "Composite variable tracking",  */
+/* Eq. 10 and Eq. 11).  Beside its size V (the volume tally), each cell  */
+/* keeps the integer sums S of its sites' coordinates, so that its       */
+/* centroid is S / V.  Under periodic boundaries a site is counted at    */
+/* the periodic image nearest a reference point of the cell: at the     */
+/* start, the cell's first site in raster order; when a copy adds or     */
+/* removes a site, the cell's centroid as the round began (the tallies   */
+/* every attempt of a round reads are those of the round's start).  The  */
+/* sums are moved by multiples of n V, so that the centroid lies in      */
+/* [0, n) on each axis, at the start and after every MCS.                */
+/* ------------------------------------------------------------------ */
+
+/* image shift k of coordinate x nearest the point S / V on an axis of
+ * extent n: x + k n is within n / 2 of S / V, k = floor((S - x V) / (n V) + 1/2) */
+static int64_t image_shift(int64_t x, int64_t S, int64_t V, int64_t n)
+{
+    return floor_div(2 * (S - x * V) + n * V, 2 * n * V);
+}
+
+static void site_coords(const orc_params *p, int64_t x, int64_t c[3])
+{
+    c[0] = x % p->nx;
+    c[1] = (x / p->nx) % p->ny;
+    c[2] = x / ((int64_t)p->nx * p->ny);
+}
+
+/* centroid of every live cell into [0, n) per axis: S -= floor(S / (n V)) n V */
+void orc_track_rewrap(const orc_params *p, const int32_t *V, int64_t *S)
+{
+    int64_t n[3] = {p->nx, p->ny, p->nz};
+    for (int64_t c = 1; c <= p->n_cells; c++) {
+        if (V[c] <= 0) continue;
+        for (int d = 0; d < p->dim; d++) {
+            int64_t nv = n[d] * V[c];
+            S[3 * c + d] -= floor_div(S[3 * c + d], nv) * nv;
+        }
+    }
+}
+
+/* sums of the lattice's cells: each site at its image nearest the cell's
+ * first site in raster order, then moved into bounds; V is the volume
+ * tally of the same lattice */
+void orc_track_init(const orc_params *p, const int32_t *lat, const int32_t *V, int64_t *S)
+{
+    int64_t nc = p->n_cells + 1, N = (int64_t)p->nx * p->ny * p->nz;
+    int64_t n[3] = {p->nx, p->ny, p->nz};
+    int64_t *anchor = (int64_t *)malloc(sizeof(int64_t) * nc);
+    for (int64_t c = 0; c < nc; c++) anchor[c] = -1;
+    memset(S, 0, sizeof(int64_t) * 3 * nc);
+    for (int64_t x = 0; x < N; x++) {
+        int32_t s = lat[x];
+        if (s <= 0) continue;
+        if (anchor[s] < 0) anchor[s] = x;
+        int64_t pc[3], ac[3];
+        site_coords(p, x, pc);
+        site_coords(p, anchor[s], ac);
+        for (int d = 0; d < p->dim; d++) S[3 * s + d] += pc[d] + n[d] * image_shift(pc[d], ac[d], 1, n[d]);
+    }
+    free(anchor);
+    orc_track_rewrap(p, V, S);
+}
+
 /* Act energy change in Q4 (1/16 energy units), rounded towards -inf */
 static int64_t delta_h_act_q(const orc_params *p, const orc_tables *tb, const int32_t *lat,
                              const uint8_t *act, int64_t i, int64_t j, int32_t si, int32_t sj, int nb,
@@ -745,9 +810,12 @@ static int replay_round(const orc_params *p, const orc_tables *tb, int32_t *lat,
     size_t nv = (size_t)(p->n_cells + 1);
     int32_t *Vs = (int32_t *)malloc(sizeof(int32_t) * nv);
     int32_t *As = (int32_t *)malloc(sizeof(int32_t) * nv);
-    if (!Vs || !As) { free(Vs); free(As); return -1; }
+    int64_t *Ss = p->csum ? (int64_t *)malloc(sizeof(int64_t) * 3 * nv) : NULL;
+    if (!Vs || !As || (p->csum && !Ss)) { free(Vs); free(As); free(Ss); return -1; }
     memcpy(Vs, V, sizeof(int32_t) * nv);
     memcpy(As, A, sizeof(int32_t) * nv);
+    if (Ss) memcpy(Ss, p->csum, sizeof(int64_t) * 3 * nv);
+    int64_t ext[3] = {p->nx, p->ny, p->nz};
 
     int64_t acc = 0;
     int64_t count = blocks ? n_blocks : nblk;
@@ -776,10 +844,19 @@ static int replay_round(const orc_params *p, const orc_tables *tb, int32_t *lat,
         if (si > 0) { V[si] += 1; A[si] += nb - 2 * mi; }
         if (sj > 0) { V[sj] -= 1; A[sj] += 2 * mj - nb; }
         if (use_act) act[j] = si > 0 ? (uint8_t)p->max_act[type_of(p, si)] : 0;
+        if (Ss) { /* site j joins sigma_i and leaves sigma_j, each at its image nearest that cell */
+            int64_t pc[3];
+            site_coords(p, j, pc);
+            for (int d = 0; d < p->dim; d++) {
+                if (si > 0) p->csum[3 * si + d] += pc[d] + ext[d] * image_shift(pc[d], Ss[3 * si + d], Vs[si], ext[d]);
+                if (sj > 0) p->csum[3 * sj + d] -= pc[d] + ext[d] * image_shift(pc[d], Ss[3 * sj + d], Vs[sj], ext[d]);
+            }
+        }
         acc++;
     }
     free(Vs);
     free(As);
+    free(Ss);
     if (accepts) *accepts += acc;
     return 0;
 }
@@ -973,6 +1050,7 @@ static int check_params(const orc_params *p)
         if (T % p->a || p->nx % (2 * T) || p->ny % (2 * T) || (p->dim == 3 && p->nz % (2 * T))) return -1;
         if (p->tile_cycles < 1 || p->P % p->tile_cycles) return -1;
         if (motility_enabled(p)) return -1; /* the tiled schedule has no motility terms */
+        if (p->csum) return -1;             /* nor composite variable tracking */
     }
     if (pers_enabled(p)) {
         for (int t = 0; t < ORC_MAXT; t++)
@@ -1007,6 +1085,7 @@ static int replay_units(const orc_params *p, int32_t *lat, uint8_t *act, int32_t
         if (++sp == per_mcs) {
             sp = 0;
             t++;
+            if (p->csum) orc_track_rewrap(p, V, p->csum);
             if (pers_enabled(p)) orc_pers_update(p, lat, t);
         }
     }
