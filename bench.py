@@ -112,7 +112,7 @@ DEFAULT_WORKLOAD = "cpm3d_tissue_1024"
 # (dram__bytes_read/write.sum) of one launch at full size, after the growth
 # burn-in and the warm-up.
 NCU_TRAFFIC = {
-    ("cpm3d_tissue_1024", "ba609db67c41"): 131.37e6 + 7.97e6,
+    ("cpm3d_tissue_1024", "e0e74b368ce0"): 131.31e6 + 7.67e6,
 }
 
 

@@ -183,6 +183,35 @@ int cpm_load_lattice(cpm_handle *h, const int32_t *src, int src_is_device);
  * Synchronises the stream. */
 int cpm_read_persistence(cpm_handle *h, double *dir);
 
+/* Composite variable tracking (Methods, "Composite variable tracking",
+ * Eq. 10 and Eq. 11): beside each cell's size V (the volume tally), the
+ * integer sums S of its sites' coordinates, so that its centroid is S / V,
+ * kept up to date by the sweep itself on every accepted copy.  Under
+ * periodic boundaries each site counts at its periodic image nearest a
+ * reference point of its cell: when tracking starts (and after
+ * cpm_load_lattice), the cell's first site in raster order; when a copy adds
+ * or removes a site, the cell's centroid as the round began (the tallies
+ * every attempt of a round reads).  At the start and after every MCS each
+ * live cell's sums are moved by a multiple of n x V so that its centroid lies
+ * in [0, n) on each axis (the paper's re-wrap); between MCS ends a centroid
+ * may leave [0, n) by the distance its cell moved.  Sums are int64 (the
+ * paper's are 32-bit, interleaved with the size for a 64-bit
+ * compare-and-swap; here size and sums are round-synchronous tallies that the
+ * round boundary keeps consistent).  The image shift of a copy must be within
+ * +-3 lattice lengths, which holds for any cell smaller than half the lattice.
+ *
+ * on = 1 allocates 48 (n_cells + 1) + 16 n_active bytes on the device,
+ * recomputes the tallies from the lattice (pending changes of the last round
+ * are folded in) and starts the sums; on = 0 frees them.  Tracking changes
+ * no lattice update.  Global schedule only: CPM_E_INVALID on a tiled handle. */
+int cpm_track_centroids(cpm_handle *h, int32_t on);
+
+/* Copy the tracked sums, (n_cells + 1) x 3 int64 (x, y, z; z is 0 in 2D;
+ * row 0, the medium, is 0) as of the last completed round, to host or device
+ * memory.  Centroid of cell c: S[c] / V[c] with V from cpm_read_tallies.
+ * CPM_E_INVALID when tracking is off.  Synchronises the stream. */
+int cpm_read_centroid_sums(cpm_handle *h, int64_t *S, int dst_is_device);
+
 /* Counters and moments of the tallies.  Synchronises the stream. */
 int cpm_stats(cpm_handle *h, cpm_stats_t *out);
 

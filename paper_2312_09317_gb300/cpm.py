@@ -70,6 +70,8 @@ _SIGNATURES = {
     "cpm_load_lattice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "cpm_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     "cpm_read_persistence": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "cpm_track_centroids": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "cpm_read_centroid_sums": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "cpm_verify": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "cpm_kernel_launches": (ctypes.c_int64, [ctypes.c_void_p]),
     "cpm_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -262,6 +264,17 @@ class Sim:
         """Persistence directions p_hat, (n_cells + 1) x 3 float64."""
         out = np.zeros((self.w.n_cells + 1, 3))
         self._check(self.lib.cpm_read_persistence(self.h, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def track_centroids(self, on: bool = True):
+        """Start (or stop) composite variable tracking (Eq. 11) of the cells'
+        coordinate sums."""
+        self._check(self.lib.cpm_track_centroids(self.h, 1 if on else 0))
+
+    def read_centroid_sums(self):
+        """Tracked coordinate sums, (n_cells + 1) x 3 int64; centroid = S / V."""
+        out = np.zeros((self.w.n_cells + 1, 3), dtype=np.int64)
+        self._check(self.lib.cpm_read_centroid_sums(self.h, ctypes.c_void_p(out.ctypes.data), 0))
         return out
 
     def load_lattice(self, src):

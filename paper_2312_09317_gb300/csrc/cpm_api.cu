@@ -55,6 +55,10 @@ struct cpm_handle {
     ObserveItem *pers_item = nullptr; // one observation item for this lattice
     int64_t *pers_cells = nullptr;    // observation rows, (n_cells + 1) x kObsFields
     int64_t *pers_member = nullptr;   // [2]
+    // composite variable tracking (Eq. 11), off until cpm_track_centroids
+    long long *csum = nullptr;        // two buffers of (n_cells + 1) x 3 coordinate sums
+    int2 *tpend = nullptr;            // two buffers of n_active: site and image shifts of a pending change
+    uint32_t *track_anchor = nullptr; // n_cells + 1 words of scratch for starting the sums
     // position
     int64_t t = 0;
     int32_t sp = 0;
@@ -95,6 +99,7 @@ uint32_t ipow(uint32_t b, int e)
 }
 
 int32_t *V_buf(cpm_handle *h, int which) { return h->tallies + (size_t)(2 * which) * (h->n_cells + 1); }
+long long *S_buf(cpm_handle *h, int which) { return h->csum + (size_t)which * 3 * (h->n_cells + 1); }
 int32_t *A_buf(cpm_handle *h, int which) { return h->tallies + (size_t)(2 * which + 1) * (h->n_cells + 1); }
 
 int validate(const cpm_config *c)
@@ -215,6 +220,13 @@ int reset_tallies(cpm_handle *h)
     CUDA_TRY(h, cudaMemcpyAsync(V_buf(h, cur ^ 1), V_buf(h, cur), bytes, cudaMemcpyDeviceToDevice, h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(A_buf(h, cur ^ 1), A_buf(h, cur), bytes, cudaMemcpyDeviceToDevice, h->stream));
     CUDA_TRY(h, cudaMemsetAsync(h->flags, 0, 2 * (size_t)h->n_active, h->stream));
+    if (h->csum) {
+        CUDA_TRY(h, launch_track_init(h->dim, h->lat, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->n_cells, V_buf(h, cur),
+                                      h->track_anchor, S_buf(h, cur), h->stream));
+        CUDA_TRY(h, cudaMemcpyAsync(S_buf(h, cur ^ 1), S_buf(h, cur), sizeof(long long) * 3 * (h->n_cells + 1),
+                                    cudaMemcpyDeviceToDevice, h->stream));
+        h->launches += 3;
+    }
     return CPM_OK;
 }
 
@@ -288,6 +300,12 @@ int run_subpass(cpm_handle *h)
         a.pend_cur = h->pend + (size_t)cur * h->n_active;
         a.flag_prev = h->flags + (size_t)(cur ^ 1) * h->n_active;
         a.flag_cur = h->flags + (size_t)cur * h->n_active;
+        if (h->csum) {
+            a.Sc = S_buf(h, cur);
+            a.Sn = S_buf(h, cur ^ 1);
+            a.tpend_prev = h->tpend + (size_t)(cur ^ 1) * h->n_active;
+            a.tpend_cur = h->tpend + (size_t)cur * h->n_active;
+        }
         CUDA_TRY(h, launch_round(h->dim, h->perim, h->act, a, h->stream));
         h->launches += 1;
         h->g += 1;
@@ -296,6 +314,13 @@ int run_subpass(cpm_handle *h)
     if (++h->sp == (int32_t)h->per_mcs) {
         h->sp = 0;
         h->t += 1;
+        if (h->csum) {
+            // every centroid back into [0, n): the same shift in both buffers
+            const int cur = (int)(h->g & 1);
+            CUDA_TRY(h, launch_track_rewrap(h->dim, h->cfg.nx, h->cfg.ny, h->cfg.nz, h->n_cells, V_buf(h, cur),
+                                            S_buf(h, cur), S_buf(h, cur ^ 1), h->stream));
+            h->launches += 1;
+        }
         if (h->pers) return pers_step(h);
     }
     return CPM_OK;
@@ -514,6 +539,9 @@ void free_all(cpm_handle *h)
     cudaFree(h->pers_item);
     cudaFree(h->pers_cells);
     cudaFree(h->pers_member);
+    cudaFree(h->csum);
+    cudaFree(h->tpend);
+    cudaFree(h->track_anchor);
     cudaFree(h->counters);
     cudaFree(h->act_tmp);
     cudaFree(h->error_flag);
@@ -751,6 +779,54 @@ int cpm_read_tallies(cpm_handle *h, int32_t *V, int32_t *A, int dst_is_device)
     const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (V) CUDA_TRY(h, cudaMemcpyAsync(V, V_buf(h, cur), bytes, kind, h->stream));
     if (A) CUDA_TRY(h, cudaMemcpyAsync(A, A_buf(h, cur), bytes, kind, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return CPM_OK;
+}
+
+int cpm_track_centroids(cpm_handle *h, int32_t on)
+{
+    if (bad(h)) return CPM_E_HANDLE;
+    if (on != 0 && on != 1) return fail(h, CPM_E_INVALID, "on must be 0 or 1");
+    if (on && h->tile) return fail(h, CPM_E_INVALID, "centroid tracking runs on the global schedule only");
+    if (int rc = check_error_flag(h)) return rc;
+    if (!on) {
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        cudaFree(h->csum);
+        cudaFree(h->tpend);
+        cudaFree(h->track_anchor);
+        h->csum = nullptr;
+        h->tpend = nullptr;
+        h->track_anchor = nullptr;
+        return CPM_OK;
+    }
+    if (h->csum) return CPM_OK;
+    const size_t nc = (size_t)h->n_cells + 1;
+    cudaError_t e = cudaMalloc(&h->csum, sizeof(long long) * 6 * nc);
+    if (e == cudaSuccess) e = cudaMalloc(&h->tpend, sizeof(int2) * 2 * (size_t)h->n_active);
+    if (e == cudaSuccess) e = cudaMalloc(&h->track_anchor, sizeof(uint32_t) * nc);
+    if (e != cudaSuccess) {
+        cudaFree(h->csum);
+        cudaFree(h->tpend);
+        cudaFree(h->track_anchor);
+        h->csum = nullptr;
+        h->tpend = nullptr;
+        h->track_anchor = nullptr;
+        return fail(h, e == cudaErrorMemoryAllocation ? CPM_E_NOMEM : CPM_E_CUDA, "cudaMalloc: %s",
+                    cudaGetErrorString(e));
+    }
+    // the tallies from the lattice into both buffers, pending changes dropped, the sums started
+    return reset_tallies(h);
+}
+
+int cpm_read_centroid_sums(cpm_handle *h, int64_t *S, int dst_is_device)
+{
+    if (bad(h)) return CPM_E_HANDLE;
+    if (!S) return fail(h, CPM_E_INVALID, "S is NULL");
+    if (!h->csum) return fail(h, CPM_E_INVALID, "centroid tracking is off (cpm_track_centroids)");
+    if (int rc = check_error_flag(h)) return rc;
+    const int cur = (int)(h->g & 1);
+    CUDA_TRY(h, cudaMemcpyAsync(S, S_buf(h, cur), sizeof(long long) * 3 * ((size_t)h->n_cells + 1),
+                                dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return CPM_OK;
 }

@@ -69,6 +69,16 @@ __host__ __device__ __forceinline__ int32_t pack_word(int32_t id, uint32_t stamp
     return (int32_t)((stamp << 24) | ((uint32_t)id & 0x00FFFFFFu));
 }
 
+// Composite variable tracking (Eq. 11): the shift k of coordinate x to its periodic image
+// nearest the point S / V on an axis of extent n, k = floor((S - x V) / (n V) + 1/2), V >= 1.
+__host__ __device__ __forceinline__ int64_t track_image_shift(int64_t x, int64_t S, int64_t V, int64_t n)
+{
+    const int64_t num = 2 * (S - x * V) + n * V, den = 2 * n * V;
+    int64_t q = num / den;
+    if (num % den != 0 && num < 0) q -= 1;
+    return q;
+}
+
 // Per-type model parameters, integer-scaled.
 struct TypeParams {
     int32_t J[kMaxTypes][kMaxTypes];
@@ -94,6 +104,13 @@ struct RoundArgs {
     int4 *pend_cur;            // accepted change of this round, per active index (written on accept only)
     const uint8_t *flag_prev;  // 1 where the previous round accepted a copy, per active index
     uint8_t *flag_cur;         // this round's flags (every active index written)
+    // composite variable tracking (Eq. 11); null when off.  Coordinate sums of every cell,
+    // [n_cells + 1][3], as of the start of this round and being built for the next round, and
+    // per active index the site and image shifts of an accepted change (valid where flagged).
+    const long long *Sc;
+    long long *Sn;
+    const int2 *tpend_prev;
+    int2 *tpend_cur;
     const uint32_t *thr;       // acceptance thresholds, L entries
     const int32_t *ln_tab;     // LN[0..128]
     const int32_t *expq;       // EXPQ[m]
@@ -241,6 +258,13 @@ cudaError_t launch_recount(int dim, const int32_t *lat, const uint8_t *cell_type
 cudaError_t launch_compare(const int32_t *V, const int32_t *A, const int32_t *V2, const int32_t *A2, int32_t n,
                            unsigned long long *n_bad, cudaStream_t st);
 cudaError_t launch_clamp_stamps(int32_t *lat, uint64_t n, uint32_t t, cudaStream_t st);
+// Composite variable tracking (csrc/cpm_track.cu): sums of a lattice's cells from scratch (anchor:
+// n_cells + 1 words of scratch), and the move of every live cell's centroid into [0, n) applied to
+// both tally buffers (V: the complete volume tally).
+cudaError_t launch_track_init(int dim, const int32_t *lat, uint32_t nx, uint32_t ny, uint32_t nz, int32_t n_cells,
+                              const int32_t *V, uint32_t *anchor, long long *S, cudaStream_t st);
+cudaError_t launch_track_rewrap(int dim, uint32_t nx, uint32_t ny, uint32_t nz, int32_t n_cells, const int32_t *V,
+                                long long *S_complete, long long *S_other, cudaStream_t st);
 cudaError_t launch_act_values(const int32_t *lat, const uint8_t *cell_type, const TypeParams &tp, uint64_t n,
                               uint32_t t_last, uint8_t *out, cudaStream_t st);
 // Lattice words <-> ids: unpack n words into ids; pack n ids into the words

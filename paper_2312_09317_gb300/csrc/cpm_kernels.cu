@@ -165,6 +165,56 @@ __device__ __noinline__ int64_t motility_q(const RoundArgs &a, int32_t si, int32
     return dh;
 }
 
+// Composite variable tracking (Eq. 11).  A copy into site j adds j to sigma_i and
+// removes it from sigma_j, each at its periodic image nearest that cell's centroid
+// as the round began (Sc / Vc); the image shifts (-3..3 per axis, 3 bits each:
+// sigma_i's in bits 0..8, sigma_j's in bits 9..17) travel with the pending change,
+// so that the next round adds the same amounts to the other buffer.
+template <int DIM>
+__device__ __noinline__ int2 track_accept(const RoundArgs &a, int32_t si, int32_t sj, uint32_t j, uint32_t jx,
+                                          uint32_t jy, uint32_t jz)
+{
+    uint32_t bits = 0;
+    const int64_t Vi = si > 0 ? a.Vc[si] : 0, Vj = sj > 0 ? a.Vc[sj] : 0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        const int64_t x = d == 0 ? jx : (d == 1 ? jy : jz);
+        const int64_t n = d == 0 ? a.nx : (d == 1 ? a.ny : a.nz);
+        if (si > 0) {
+            const int64_t k = track_image_shift(x, a.Sc[3 * si + d], Vi, n);
+            atomicAdd((unsigned long long *)(a.Sn + 3 * si + d), (unsigned long long)(x + n * k));
+            bits |= (uint32_t)(k + 3) << (3 * d);
+        }
+        if (sj > 0) {
+            const int64_t k = track_image_shift(x, a.Sc[3 * sj + d], Vj, n);
+            atomicAdd((unsigned long long *)(a.Sn + 3 * sj + d), (unsigned long long)(-(x + n * k)));
+            bits |= (uint32_t)(k + 3) << (9 + 3 * d);
+        }
+    }
+    return make_int2((int32_t)j, (int32_t)bits);
+}
+
+// the previous round's tracked change (see track_accept) into the other buffer
+template <int DIM>
+__device__ __noinline__ void track_carry(const RoundArgs &a, int32_t si, int32_t sj, int2 e)
+{
+    const uint32_t j = (uint32_t)e.x, bits = (uint32_t)e.y;
+    const uint32_t jx = j % a.nx, jy = (j / a.nx) % a.ny, jz = j / (a.nx * a.ny);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        const int64_t x = d == 0 ? jx : (d == 1 ? jy : jz);
+        const int64_t n = d == 0 ? a.nx : (d == 1 ? a.ny : a.nz);
+        if (si > 0) {
+            const int64_t k = (int64_t)((bits >> (3 * d)) & 7u) - 3;
+            atomicAdd((unsigned long long *)(a.Sn + 3 * si + d), (unsigned long long)(x + n * k));
+        }
+        if (sj > 0) {
+            const int64_t k = (int64_t)((bits >> (9 + 3 * d)) & 7u) - 3;
+            atomicAdd((unsigned long long *)(a.Sn + 3 * sj + d), (unsigned long long)(-(x + n * k)));
+        }
+    }
+}
+
 // One copy attempt of active block (ix, iy, iz) (active index i) in the round
 // described by a; also carries the previous round's change of index i into
 // the next tallies.  Returns whether the copy was accepted.
@@ -183,7 +233,7 @@ __device__ __noinline__ int64_t motility_q(const RoundArgs &a, int32_t si, int32
 // rolls the geometric mean like the neighbour sum.  Level 0 (kernels without
 // Act) stays fully unrolled.  The level changes only the code layout: every
 // sum visits the same sites, and integer sums do not depend on the order.
-template <int DIM, bool PERIM, bool ACT, int ROLL>
+template <int DIM, bool PERIM, bool ACT, int ROLL, bool TRACK = false>
 __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTables &sm, uint32_t ix, uint32_t iy,
                                               uint32_t iz, uint32_t i)
 {
@@ -219,6 +269,7 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
             const int4 e = a.pend_prev[i];
             if (e.x > 0) { atomicAdd(a.Vn + e.x, 1); atomicAdd(a.An + e.x, e.z); }
             if (e.y > 0) { atomicAdd(a.Vn + e.y, -1); atomicAdd(a.An + e.y, e.w); }
+            if (TRACK) track_carry<DIM>(a, e.x, e.y, a.tpend_prev[i]);
         }
         const int32_t wj = lat_word<ACT>(a, j);
         const int32_t sj = cell_id(wj);
@@ -313,6 +364,7 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
                     if (si > 0) { atomicAdd(a.Vn + si, 1); atomicAdd(a.An + si, dAi); }
                     if (sj > 0) { atomicAdd(a.Vn + sj, -1); atomicAdd(a.An + sj, dAj); }
                     a.pend_cur[i] = make_int4(si, sj, dAi, dAj);
+                    if (TRACK) a.tpend_cur[i] = track_accept<DIM>(a, si, sj, j, jx, jy, jz);
                     accepted = true;
                 }
             }
@@ -334,7 +386,9 @@ __device__ __forceinline__ bool round_attempt(const RoundArgs &a, const SmemTabl
 #define CPM_ROUND_MIN_BLOCKS_ACT 8
 #endif
 
-template <int DIM, bool PERIM, bool ACT>
+// TRACK: composite variable tracking on (a.Sc, a.Sn, a.tpend_* set), a kernel
+// of its own so that the sweep without it carries none of its code
+template <int DIM, bool PERIM, bool ACT, bool TRACK>
 __global__ void __launch_bounds__(kThreads, ACT ? CPM_ROUND_MIN_BLOCKS_ACT : CPM_ROUND_MIN_BLOCKS)
     round_kernel(const RoundArgs a)
 {
@@ -359,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, ACT ? CPM_ROUND_MIN_BLOCKS_ACT : CPM
     const uint32_t i = ix + a.nax * (iy + a.nay * iz);
     bool accepted = false;
     if (valid) {
-        accepted = round_attempt<DIM, PERIM, ACT, ACT ? 1 : 0>(a, sm, ix, iy, iz, i);
+        accepted = round_attempt<DIM, PERIM, ACT, ACT ? 1 : 0, TRACK>(a, sm, ix, iy, iz, i);
     }
     const unsigned m = __ballot_sync(0xffffffffu, accepted);
     if ((threadIdx.x & 31) == 0 && m != 0) atomicAdd(a.accepts, (unsigned long long)__popc(m));
@@ -640,7 +694,7 @@ unsigned grid_for(uint64_t n, unsigned threads)
     return (unsigned)(g == 0 ? 1 : g);
 }
 
-template <int DIM, bool PERIM, bool ACT>
+template <int DIM, bool PERIM, bool ACT, bool TRACK>
 cudaError_t launch_round_t(const RoundArgs &a, cudaStream_t st)
 {
     const uint32_t naz = a.n_active / (a.nax * a.nay);
@@ -649,7 +703,7 @@ cudaError_t launch_round_t(const RoundArgs &a, cudaStream_t st)
                             ((naz + bz - 1) / bz);
     const unsigned threads = a.brick_x * a.brick_y * bz;
     if (!a.pdl) {
-        round_kernel<DIM, PERIM, ACT><<<blocks, threads, 0, st>>>(a);
+        round_kernel<DIM, PERIM, ACT, TRACK><<<blocks, threads, 0, st>>>(a);
         return cudaGetLastError();
     }
     // programmatic dependent launch: the CTAs of this round may start while the
@@ -665,7 +719,13 @@ cudaError_t launch_round_t(const RoundArgs &a, cudaStream_t st)
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, round_kernel<DIM, PERIM, ACT>, a);
+    return cudaLaunchKernelEx(&cfg, round_kernel<DIM, PERIM, ACT, TRACK>, a);
+}
+
+template <int DIM, bool PERIM, bool ACT>
+cudaError_t launch_round_t(const RoundArgs &a, cudaStream_t st)
+{
+    return a.Sc ? launch_round_t<DIM, PERIM, ACT, true>(a, st) : launch_round_t<DIM, PERIM, ACT, false>(a, st);
 }
 
 }  // namespace

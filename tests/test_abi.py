@@ -109,6 +109,8 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.cpm_step(None, 1) == cpm.CPM_E_HANDLE
     assert lib.cpm_read_lattice(None, None, 0) == cpm.CPM_E_HANDLE
     assert lib.cpm_kernel_launches(None) == 0
+    assert lib.cpm_track_centroids(None, 1) == cpm.CPM_E_HANDLE
+    assert lib.cpm_read_centroid_sums(None, None, 0) == cpm.CPM_E_HANDLE
     lib.cpm_destroy(None)
 
 
