@@ -270,8 +270,20 @@ int cpm_batch_step(cpm_batch *b, int64_t n_mcs);
  *   on = 2: a test of that path: as on = 1, but the launch's first CTA leaves
  *          before its first barrier, so the other CTAs' waits run out (use a
  *          small max_polls); the step returns CPM_E_STATE.
- * Errors: CPM_E_HANDLE, CPM_E_INVALID (on not 0..2), CPM_E_CUDA. */
+ * Errors: CPM_E_HANDLE, CPM_E_INVALID (on not 0..2, or on != 0 while the
+ * batch tracks centroids), CPM_E_CUDA. */
 int cpm_batch_set_persistent(cpm_batch *b, int32_t on, int64_t max_polls);
+
+/* Composite variable tracking (as cpm_track_centroids) in every lattice of
+ * the batch: on = 1 starts it (tallies recomputed from each lattice, pending
+ * changes folded in), on = 0 stops it.  The batch graph then runs the
+ * tracking variant of the round kernel and, after each MCS, moves every
+ * member's centroids into [0, n).  Graph loop only: CPM_E_INVALID while the
+ * persistent loop is on.  cpm_batch_read_centroid_sums copies lattice idx's
+ * sums as cpm_read_centroid_sums does (CPM_E_INVALID when tracking is off or
+ * idx is out of range). */
+int cpm_batch_track_centroids(cpm_batch *b, int32_t on);
+int cpm_batch_read_centroid_sums(cpm_batch *b, int32_t idx, int64_t *S, int dst_is_device);
 
 /* Pick the CTA brick shape (active blocks per CTA along x, y, z) for this
  * batch by timing: in 1 + n_mcs_each passes every candidate shape runs one

@@ -71,6 +71,8 @@ _SIGNATURES = {
     "cpm_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     "cpm_read_persistence": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "cpm_track_centroids": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "cpm_batch_track_centroids": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "cpm_batch_read_centroid_sums": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int]),
     "cpm_read_centroid_sums": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "cpm_verify": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "cpm_kernel_launches": (ctypes.c_int64, [ctypes.c_void_p]),
@@ -355,6 +357,15 @@ class Batch:
     def load_lattice(self, idx: int, src):
         p, dev = _ptr(src)
         self._check(self.lib.cpm_batch_load_lattice(self.b, idx, ctypes.c_void_p(p), dev))
+
+    def track_centroids(self, on: bool = True):
+        """Composite variable tracking (Eq. 11) in every lattice of the batch."""
+        self._check(self.lib.cpm_batch_track_centroids(self.b, 1 if on else 0))
+
+    def read_centroid_sums(self, idx: int):
+        out = np.zeros((self.ws[idx].n_cells + 1, 3), dtype=np.int64)
+        self._check(self.lib.cpm_batch_read_centroid_sums(self.b, idx, ctypes.c_void_p(out.ctypes.data), 0))
+        return out
 
     def read_tallies(self, idx: int):
         w = self.ws[idx]

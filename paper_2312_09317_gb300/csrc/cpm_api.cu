@@ -996,6 +996,7 @@ struct cpm_batch {
     unsigned *d_next = nullptr;          // per-round item counters of the persistent loop
     int *d_err = nullptr;                // barrier timeout flag
     uint32_t loop_grid = 0;              // CTAs of the last persistent launch
+    bool track = false;                  // composite variable tracking in every member
     bool descriptors_dirty = true;
     int64_t launches = 0;
     std::string err;
@@ -1109,12 +1110,16 @@ int batch_build_graph(cpm_batch *b)
     size_t active = b->order.size();
     for (uint32_t q = 0; q < r_max && e == cudaSuccess; q++) {
         while (active > 0 && b->lats[b->order[active - 1]].R <= q) active--;
-        e = launch_batch_round(b->dim, b->perim, b->act, b->d_lats, b->d_items, b->items_upto[active], q,
+        e = launch_batch_round(b->dim, b->perim, b->act, b->track, b->d_lats, b->d_items, b->items_upto[active], q,
                                batch_threads(b), b->capture_stream);
         n++;
     }
     if (e == cudaSuccess) {
         e = launch_batch_advance(b->d_lats, (uint32_t)b->lats.size(), b->capture_stream);
+        n++;
+    }
+    if (e == cudaSuccess && b->track) {
+        e = launch_batch_track_rewrap(b->dim, b->d_lats, (uint32_t)b->lats.size(), b->capture_stream);
         n++;
     }
     cudaGraph_t g = nullptr;
@@ -1227,6 +1232,7 @@ int cpm_batch_create(const cpm_config *cfgs, int32_t n, void *cuda_stream, cpm_b
         L.k = h->k;
         L.C = h->C;
         L.R = h->per_sub_mcs * h->k;
+        L.n_cells = h->n_cells;
         b->lats.push_back(L);
     }
     b->order.resize(n);
@@ -1339,9 +1345,38 @@ int cpm_batch_set_persistent(cpm_batch *b, int32_t on, int64_t max_polls)
         if (e != cudaSuccess) return bfail(b, CPM_E_CUDA, cudaGetErrorString(e));
     }
     if (on < 0 || on > 2) return bfail(b, CPM_E_INVALID, "on must be 0, 1 or 2");
+    if (on != 0 && b->track) return bfail(b, CPM_E_INVALID, "the persistent loop does not track centroids");
     b->persistent = on != 0;
     b->test_absent = on == 2;
     b->max_polls = max_polls >= 0 ? (long long)max_polls : (1ll << 24);
+    return CPM_OK;
+}
+
+int cpm_batch_track_centroids(cpm_batch *b, int32_t on)
+{
+    if (!b) return CPM_E_HANDLE;
+    if (on != 0 && on != 1) return bfail(b, CPM_E_INVALID, "on must be 0 or 1");
+    if (on && b->persistent) return bfail(b, CPM_E_INVALID, "the persistent loop does not track centroids");
+    for (size_t l = 0; l < b->hs.size(); l++) {
+        cpm_handle *h = b->hs[l];
+        if (int rc = cpm_track_centroids(h, on))
+            return bfail(b, rc, "lattice " + std::to_string(l) + ": " + cpm_last_error(h));
+        for (int p = 0; p < 2; p++) {
+            b->lats[l].S[p] = on ? S_buf(h, p) : nullptr;
+            b->lats[l].tpend[p] = on ? h->tpend + (size_t)p * h->n_active : nullptr;
+        }
+    }
+    b->track = on != 0;
+    b->descriptors_dirty = true;
+    batch_drop_graph(b);
+    return CPM_OK;
+}
+
+int cpm_batch_read_centroid_sums(cpm_batch *b, int32_t idx, int64_t *S, int dst_is_device)
+{
+    if (!b) return CPM_E_HANDLE;
+    if (idx < 0 || idx >= (int32_t)b->hs.size()) return bfail(b, CPM_E_INVALID, "idx out of range");
+    if (int rc = cpm_read_centroid_sums(b->hs[idx], S, dst_is_device)) return bfail(b, rc, cpm_last_error(b->hs[idx]));
     return CPM_OK;
 }
 

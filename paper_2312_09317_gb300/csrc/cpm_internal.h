@@ -140,12 +140,17 @@ struct BatchLattice {
     int32_t *V[2], *A[2];
     int4 *pend[2];
     uint8_t *flag[2];
-    uint32_t R, k, C, pad_;
+    long long *S[2];     // tracked centroid sums, when the batch tracks them (else null)
+    int2 *tpend[2];
+    uint32_t R, k, C;
+    int32_t n_cells;
     int64_t t_start;
     uint64_t g_start;
 };
-cudaError_t launch_batch_round(int dim, bool perim, bool act, const BatchLattice *lats, const int2 *items,
-                               uint32_t n_items, uint32_t q, uint32_t threads, cudaStream_t st);
+cudaError_t launch_batch_round(int dim, bool perim, bool act, bool track, const BatchLattice *lats,
+                               const int2 *items, uint32_t n_items, uint32_t q, uint32_t threads, cudaStream_t st);
+// every tracking member's centroids into [0, n) after its MCS (csrc/cpm_track.cu)
+cudaError_t launch_batch_track_rewrap(int dim, const BatchLattice *lats, uint32_t n, cudaStream_t st);
 cudaError_t launch_batch_clamp(const BatchLattice *lats, const int2 *items, uint32_t n_items, cudaStream_t st);
 cudaError_t launch_batch_advance(BatchLattice *lats, uint32_t n, cudaStream_t st);
 // The persistent batched MCS loop (one cooperative launch for n_mcs MCS).

@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(kThreads, ACT ? CPM_ROUND_MIN_BLOCKS_ACT : CPM
 // One (lattice, brick) item of batch round q: lattice it.x's round number
 // g_start + q, exactly as the single-lattice round kernel would run it (same
 // colour, counters and tallies).  ra and sm are the CTA's shared set-up.
-template <int DIM, bool PERIM, bool ACT>
+template <int DIM, bool PERIM, bool ACT, bool TRACK = false>
 __device__ __forceinline__ void batch_round_item(RoundArgs &ra, SmemTables &sm, const BatchLattice *lats, int2 it,
                                                  uint32_t q)
 {
@@ -471,6 +471,12 @@ __device__ __forceinline__ void batch_round_item(RoundArgs &ra, SmemTables &sm, 
         ra.pend_cur = L.pend[par];
         ra.flag_prev = L.flag[par ^ 1u];
         ra.flag_cur = L.flag[par];
+        if (TRACK) {
+            ra.Sc = L.S[par];
+            ra.Sn = L.S[par ^ 1u];
+            ra.tpend_prev = L.tpend[par ^ 1u];
+            ra.tpend_cur = L.tpend[par];
+        }
     }
     __syncthreads();
     load_tables(sm, ra, ACT);
@@ -487,7 +493,7 @@ __device__ __forceinline__ void batch_round_item(RoundArgs &ra, SmemTables &sm, 
     bool accepted = false;
     if (threadIdx.x < bx_ * by_ * bz_ && ix < ra.nax && iy < ra.nay && iz < naz) {
         const uint32_t i = ix + ra.nax * (iy + ra.nay * iz);
-        accepted = round_attempt<DIM, PERIM, ACT, ACT ? (DIM == 3 ? 2 : 1) : 0>(ra, sm, ix, iy, iz, i);
+        accepted = round_attempt<DIM, PERIM, ACT, ACT ? (DIM == 3 ? 2 : 1) : 0, TRACK>(ra, sm, ix, iy, iz, i);
     }
     const unsigned m = __ballot_sync(0xffffffffu, accepted);
     if ((threadIdx.x & 31) == 0 && m != 0) atomicAdd(ra.accepts, (unsigned long long)__popc(m));
@@ -503,13 +509,14 @@ __device__ __forceinline__ void batch_round_item(RoundArgs &ra, SmemTables &sm, 
 #ifndef CPM_BATCH_MIN_BLOCKS_ACT
 #define CPM_BATCH_MIN_BLOCKS_ACT 8
 #endif
-template <int DIM, bool PERIM, bool ACT>
+// TRACK: every member keeps its tracked centroid sums (BatchLattice::S)
+template <int DIM, bool PERIM, bool ACT, bool TRACK>
 __global__ void __launch_bounds__(kBatchMaxThreads, ACT ? CPM_BATCH_MIN_BLOCKS_ACT : CPM_BATCH_MIN_BLOCKS)
     batch_round_kernel(const BatchLattice *lats, const int2 *items, uint32_t q)
 {
     __shared__ RoundArgs ra;
     __shared__ SmemTables sm;
-    batch_round_item<DIM, PERIM, ACT>(ra, sm, lats, items[blockIdx.x], q);
+    batch_round_item<DIM, PERIM, ACT, TRACK>(ra, sm, lats, items[blockIdx.x], q);
 }
 
 // Stamps whose age is 128 or more are reset to age exactly 128, so that ages
@@ -810,26 +817,33 @@ cudaError_t launch_batch_loop(int dim, bool perim, bool act, const BatchLoopArgs
                  : launch_batch_loop_t<3, false, false>(p, threads, st, grid_out);
 }
 
-cudaError_t launch_batch_round(int dim, bool perim, bool act, const BatchLattice *lats, const int2 *items,
-                               uint32_t n_items, uint32_t q, uint32_t threads, cudaStream_t st)
+template <int DIM, bool PERIM, bool ACT>
+void batch_round_t(bool track, const BatchLattice *lats, const int2 *items, uint32_t n_items, uint32_t q,
+                   uint32_t threads, cudaStream_t st)
+{
+    if (track) batch_round_kernel<DIM, PERIM, ACT, true><<<n_items, threads, 0, st>>>(lats, items, q);
+    else batch_round_kernel<DIM, PERIM, ACT, false><<<n_items, threads, 0, st>>>(lats, items, q);
+}
+
+cudaError_t launch_batch_round(int dim, bool perim, bool act, bool track, const BatchLattice *lats,
+                               const int2 *items, uint32_t n_items, uint32_t q, uint32_t threads, cudaStream_t st)
 {
     if (n_items == 0) return cudaSuccess;
-    const uint32_t kBatchThreads = threads;
     if (dim == 2) {
         if (act) {
-            if (perim) batch_round_kernel<2, true, true><<<n_items, kBatchThreads, 0, st>>>(lats, items, q);
-            else batch_round_kernel<2, false, true><<<n_items, kBatchThreads, 0, st>>>(lats, items, q);
+            if (perim) batch_round_t<2, true, true>(track, lats, items, n_items, q, threads, st);
+            else batch_round_t<2, false, true>(track, lats, items, n_items, q, threads, st);
         } else {
-            if (perim) batch_round_kernel<2, true, false><<<n_items, kBatchThreads, 0, st>>>(lats, items, q);
-            else batch_round_kernel<2, false, false><<<n_items, kBatchThreads, 0, st>>>(lats, items, q);
+            if (perim) batch_round_t<2, true, false>(track, lats, items, n_items, q, threads, st);
+            else batch_round_t<2, false, false>(track, lats, items, n_items, q, threads, st);
         }
     } else {
         if (act) {
-            if (perim) batch_round_kernel<3, true, true><<<n_items, kBatchThreads, 0, st>>>(lats, items, q);
-            else batch_round_kernel<3, false, true><<<n_items, kBatchThreads, 0, st>>>(lats, items, q);
+            if (perim) batch_round_t<3, true, true>(track, lats, items, n_items, q, threads, st);
+            else batch_round_t<3, false, true>(track, lats, items, n_items, q, threads, st);
         } else {
-            if (perim) batch_round_kernel<3, true, false><<<n_items, kBatchThreads, 0, st>>>(lats, items, q);
-            else batch_round_kernel<3, false, false><<<n_items, kBatchThreads, 0, st>>>(lats, items, q);
+            if (perim) batch_round_t<3, true, false>(track, lats, items, n_items, q, threads, st);
+            else batch_round_t<3, false, false>(track, lats, items, n_items, q, threads, st);
         }
     }
     return cudaGetLastError();

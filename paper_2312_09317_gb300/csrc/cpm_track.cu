@@ -53,12 +53,10 @@ __device__ __forceinline__ int64_t floor_div_p(int64_t a, int64_t b)
     return q;
 }
 
-// one thread per cell id 1..n_cells; S_other may be null
-__global__ void track_rewrap_kernel(int dim, uint32_t nx, uint32_t ny, uint32_t nz, int32_t n_cells,
-                                    const int32_t *V, long long *S_complete, long long *S_other)
+// cell c's centroid into [0, n): the shift from the complete buffer, applied to both
+__device__ __forceinline__ void rewrap_cell(int dim, uint32_t nx, uint32_t ny, uint32_t nz, int32_t c,
+                                            const int32_t *V, long long *S_complete, long long *S_other)
 {
-    const int32_t c = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x) + 1;
-    if (c > n_cells) return;
     const int64_t v = V[c];
     if (v <= 0) return;
     for (int d = 0; d < dim; ++d) {
@@ -68,6 +66,25 @@ __global__ void track_rewrap_kernel(int dim, uint32_t nx, uint32_t ny, uint32_t 
         S_complete[3 * c + d] -= shift;
         if (S_other) S_other[3 * c + d] -= shift;
     }
+}
+
+// one thread per cell id 1..n_cells; S_other may be null
+__global__ void track_rewrap_kernel(int dim, uint32_t nx, uint32_t ny, uint32_t nz, int32_t n_cells,
+                                    const int32_t *V, long long *S_complete, long long *S_other)
+{
+    const int32_t c = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x) + 1;
+    if (c <= n_cells) rewrap_cell(dim, nx, ny, nz, c, V, S_complete, S_other);
+}
+
+// one CTA per batch member, after the advance of its MCS and round counters:
+// buffer g_start & 1 is then the complete one
+__global__ void batch_track_rewrap_kernel(int dim, const BatchLattice *lats)
+{
+    const BatchLattice &L = lats[blockIdx.x];
+    if (!L.S[0]) return;
+    const uint32_t par = (uint32_t)(L.g_start & 1u);
+    for (int32_t c = (int32_t)threadIdx.x + 1; c <= L.n_cells; c += (int32_t)blockDim.x)
+        rewrap_cell(dim, L.base.nx, L.base.ny, L.base.nz, c, L.V[par], L.S[par], L.S[par ^ 1u]);
 }
 
 unsigned grid_of(uint64_t n)
@@ -85,6 +102,13 @@ cudaError_t launch_track_rewrap(int dim, uint32_t nx, uint32_t ny, uint32_t nz, 
     if (n_cells <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)(((uint32_t)n_cells + kTrackThreads - 1) / kTrackThreads);
     track_rewrap_kernel<<<blocks, kTrackThreads, 0, st>>>(dim, nx, ny, nz, n_cells, V, S_complete, S_other);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_track_rewrap(int dim, const BatchLattice *lats, uint32_t n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    batch_track_rewrap_kernel<<<n, kTrackThreads, 0, st>>>(dim, lats);
     return cudaGetLastError();
 }
 

@@ -96,3 +96,57 @@ def test_tracking_started_mid_run_and_after_a_load(cpm):
     with pytest.raises(cpm.CPMError):
         sim.read_centroid_sums()
     sim.close()
+
+
+def _batch_members():
+    w2 = cw.random_small(22, dim=2, n=32, n_cells=14, edge=3, act=True, a=8, c=2, P=4)
+    return [drifting(2, 21, True),
+            cw.with_motility(w2, chem=cw.uniform_field((1, 32, 32), 2, (0.3, 1.0)), lambda_chem=300),
+            drifting(2, 23, True)]
+
+
+def test_tracked_sums_in_a_batch(cpm):
+    """Members of uneven sizes and rounds per MCS, each bit-exact with its
+    own replay, sums included; the persistent loop refuses tracking."""
+    ws = _batch_members()
+    b = cpm.Batch(ws)
+    b.track_centroids(True)
+    with pytest.raises(cpm.CPMError):
+        b.set_persistent(True)
+    refs = [oracle.State(w, track=True) for w in ws]
+    for i, r in enumerate(refs):
+        assert np.array_equal(b.read_centroid_sums(i), r.csum)
+    for n in (1, 2, 3):
+        b.step(n)
+        for i, r in enumerate(refs):
+            r.replay_run(n)
+            assert np.array_equal(b.read_lattice(i), r.lattice), i
+            V, A = b.read_tallies(i)
+            assert np.array_equal(V, r.V) and np.array_equal(A, r.A), i
+            assert np.array_equal(b.read_centroid_sums(i), r.csum), i
+    b.close()
+
+
+def test_batch_tracking_started_after_steps(cpm):
+    ws = _batch_members()
+    b = cpm.Batch(ws)
+    b.step(2)
+    b.track_centroids(True)
+    refs = [oracle.State(w) for w in ws]
+    for i, r in enumerate(refs):
+        assert np.array_equal(b.read_centroid_sums(i), r.track_sums_of(b.read_lattice(i))), i
+    b.step(3)
+    for i, w in enumerate(ws):
+        lat = b.read_lattice(i)
+        S = b.read_centroid_sums(i)
+        V, _ = b.read_tallies(i)
+        S_b, cnt = brute_sums(w, lat, S)
+        live = cnt > 0
+        live[0] = False
+        assert np.array_equal(V[live], cnt[live]), i
+        assert np.array_equal(S[live], S_b[live]), i
+    b.track_centroids(False)
+    with pytest.raises(cpm.CPMError):
+        b.read_centroid_sums(0)
+    b.step(1)
+    b.close()
