@@ -15,6 +15,8 @@ The arithmetic lives in ``cpm_oracle.c`` (plain C, compiled with gcc by
   the integer threshold table.
 * ``replay_blocks`` -- one round of (b) restricted to a list of blocks, for
   sampled checks.
+* ``State(w, track=True)`` -- (b) with composite variable tracking (Eq. 10,
+  Eq. 11): per-cell coordinate sums in ``State.csum``.
 """
 from __future__ import annotations
 

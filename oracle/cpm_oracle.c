@@ -29,7 +29,9 @@
  *      counted by (block, attempt, MCS, sub-pass), so the replay draws exactly
  *      what any parallel execution of the scheme draws.  Energies are exact
  *      integers (Act in Q4 fixed point) and acceptance compares a uint32 draw
- *      with an integer threshold table.
+ *      with an integer threshold table.  With params.csum set the replay also
+ *      keeps every cell's coordinate sums (composite variable tracking,
+ *      Methods, Eq. 10 and Eq. 11; orc_track_init, orc_track_rewrap).
  *
  * Conventions (data, identical for every consumer): lattice x-fastest; id 0
  * is the medium (type 0), ids > 0 are cells, id -1 is a frozen obstacle of
