@@ -88,9 +88,15 @@ def drifting(dim, seed, act):
     return cw.with_motility(w, chem=f, lambda_chem=400)
 
 
-@pytest.mark.parametrize("dim,seed,act", [(2, 3, False), (2, 4, True), (3, 5, True)])
+def obstructed_3d():
+    """3D cells among frozen obstacle sites on 8^3 areas (a second block size and schedule)."""
+    w = cw.random_small(12, dim=3, n=16, n_cells=10, edge=3, act=True, obstacles=0.04, a=8, c=2, P=16)
+    return cw.with_motility(w, chem=cw.uniform_field((16, 16, 16), 3, (0.2, 1.0, 0.5)), lambda_chem=300)
+
+
+@pytest.mark.parametrize("dim,seed,act", [(2, 3, False), (2, 4, True), (3, 5, True), (3, 0, True)])
 def test_tracked_sums_follow_the_lattice(dim, seed, act):
-    w = drifting(dim, seed, act)
+    w = drifting(dim, seed, act) if seed else obstructed_3d()
     st = oracle.State(w, track=True)
     plain = oracle.State(w)
     per = st.subpasses_per_mcs()
